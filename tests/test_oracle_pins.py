@@ -1,0 +1,382 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test names what it pins and why a plausible mistake would fail it.
+No GPU, no CUDA library.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_03207_gb300 import synthetic as S
+
+C0 = 0.5 / math.sqrt(math.pi)
+
+
+def _scene(n, means, log_scales, quats=None, logits=None, sh=None):
+    quats = np.tile([1.0, 0, 0, 0], (n, 1)) if quats is None else quats
+    logits = np.full(n, 2.0) if logits is None else logits
+    if sh is None:
+        sh = np.zeros((n, 16, 3))
+        sh[:, 0, :] = 0.5 / C0  # colour exactly 1 in every channel
+    return {"means": np.asarray(means, float).reshape(n, 3),
+            "log_scales": np.asarray(log_scales, float).reshape(n, 3),
+            "quats": np.asarray(quats, float).reshape(n, 4),
+            "opacity_logits": np.asarray(logits, float).reshape(n), "sh": np.asarray(sh, float)}
+
+
+def _cam(w=64, h=64, f=64.0, viewmat=None, bg=(0.0, 0.0, 0.0)):
+    vm = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], float) if viewmat is None else viewmat
+    return {"viewmat": vm, "fx": f, "fy": f, "cx": w / 2, "cy": h / 2, "width": w, "height": h,
+            "znear": 0.2, "bg": bg}
+
+
+# ------------------------------------------------------------------ SH (§2.1)
+
+def _sphere_quadrature(nz=8, nphi=16):
+    z, wz = np.polynomial.legendre.leggauss(nz)
+    phi = (np.arange(nphi) + 0.5) * 2 * np.pi / nphi
+    pts, wts = [], []
+    for zi, wi in zip(z, wz):
+        st = math.sqrt(1 - zi * zi)
+        for p in phi:
+            pts.append((st * math.cos(p), st * math.sin(p), zi))
+            wts.append(wi * 2 * np.pi / nphi)
+    return np.array(pts), np.array(wts)
+
+
+def test_sh_orthonormal_exact_quadrature():
+    """The 16 basis functions are orthonormal on the sphere. Gauss-Legendre in
+    cos(theta) x uniform phi integrates their products exactly; a wrong
+    normalisation constant, factorial or recurrence breaks this."""
+    pts, wts = _sphere_quadrature()
+    Y = np.array([oracle.sh_basis(p) for p in pts])
+    gram = (Y * wts[:, None]).T @ Y
+    np.testing.assert_allclose(gram, np.eye(16), atol=1e-12)
+
+
+def test_sh_addition_theorem():
+    """Addition theorem: sum_m Y_lm(d)^2 = (2l+1)/(4 pi) for every direction
+    and band (so every band is complete and rotation invariant)."""
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        Y = oracle.sh_basis(d)
+        for l in range(4):
+            band = Y[l * l:(l + 1) * (l + 1)]
+            assert abs(np.sum(band ** 2) - (2 * l + 1) / (4 * math.pi)) < 1e-12
+
+
+def test_sh_pole_values_and_phase_convention():
+    """At d = +z only m = 0 survives with value sqrt((2l+1)/4pi). The
+    Condon-Shortley phase makes the l = 1 functions -y, z, -x (3DGS/PLY
+    coefficient convention)."""
+    Y = oracle.sh_basis([0, 0, 1])
+    for l in range(4):
+        for m in range(-l, l + 1):
+            expect = math.sqrt((2 * l + 1) / (4 * math.pi)) if m == 0 else 0.0
+            assert abs(Y[l * l + l + m] - expect) < 1e-14
+    k1 = math.sqrt(3 / (4 * math.pi))
+    np.testing.assert_allclose(oracle.sh_basis([1, 0, 0])[1:4], [0, 0, -k1], atol=1e-14)
+    np.testing.assert_allclose(oracle.sh_basis([0, 1, 0])[1:4], [-k1, 0, 0], atol=1e-14)
+
+
+def test_sh_cartesian_form_matches_definition_and_gradient():
+    """The Cartesian polynomials used by the backward equal the Legendre
+    definition on the sphere, and their gradients match central differences."""
+    rng = np.random.default_rng(12)
+    for _ in range(40):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        y_def = oracle.sh_basis(d)
+        y_cart, g = oracle.sh_basis_cart(d)
+        np.testing.assert_allclose(y_cart, y_def, atol=1e-13)
+        h = 1e-6
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            fd = (oracle.sh_basis_cart(d + e)[0] - oracle.sh_basis_cart(d - e)[0]) / (2 * h)
+            np.testing.assert_allclose(g[:, a], fd, atol=1e-8)
+
+
+# -------------------------------------------------------- preprocess (§3.2)
+
+def test_isotropic_on_axis_closed_form():
+    """Isotropic s at (0, 0, z), camera at the origin: Sigma' = ((f s / z)^2 +
+    0.3) I, conic its inverse, centre at the principal point, and the extent
+    where alpha = 1/255 is sqrt(2 ln(255 sigma) Sigma'_xx) (§3.4)."""
+    z, s, f, logit = 4.0, 0.05, 64.0, 1.0
+    sc = _scene(1, [0, 0, z], [math.log(s)] * 3, logits=[logit])
+    p = oracle.preprocess(sc, _cam(f=f))
+    v = (f * s / z) ** 2 + 0.3
+    np.testing.assert_allclose(p["cov2d"][0], [v, 0, v], rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(p["conic"][0], [1 / v, 0, 1 / v], rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(p["mean2d"][0], [32, 32], atol=1e-13)
+    sigma = 1 / (1 + math.exp(-logit))
+    e = math.sqrt(2 * math.log(255 * sigma) * v)
+    np.testing.assert_allclose(p["extent"][0], [e, e], rtol=1e-13)
+    assert p["depth"][0] == np.float32(z)
+    np.testing.assert_allclose(p["rgb"][0], [1, 1, 1], rtol=1e-14)
+    assert p["reason"][0] == 0
+
+
+def test_isotropic_off_axis_closed_form():
+    """Isotropic s at (x, 0, z): J = [[f/z, 0, -f x/z^2], [0, f/z, 0]] gives
+    Sigma'_xx = s^2 f^2/z^2 (1 + x^2/z^2) + 0.3, Sigma'_yy = s^2 f^2/z^2 + 0.3;
+    past the guard band the ratio x/z is clamped inside J only."""
+    f, s, z = 64.0, 0.05, 4.0
+    for x in (1.0, -1.5):
+        sc = _scene(1, [x, 0, z], [math.log(s)] * 3)
+        p = oracle.preprocess(sc, _cam(f=f))
+        k = (s * f / z) ** 2
+        np.testing.assert_allclose(p["cov2d"][0], [k * (1 + x * x / z / z) + 0.3, 0, k + 0.3], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(p["mean2d"][0], [f * x / z + 32, 32], rtol=1e-14)
+    # x/z = 2 > 1.3 * (W/2)/f = 0.65: the Jacobian uses 0.65
+    sc = _scene(1, [8.0, 0, z], [math.log(s)] * 3)
+    p = oracle.preprocess(sc, _cam(f=f))
+    k = (s * f / z) ** 2
+    np.testing.assert_allclose(p["cov2d"][0, 0], k * (1 + 0.65 ** 2) + 0.3, rtol=1e-12)
+
+
+def test_general_covariance_against_numerical_jacobian():
+    """Sigma' = J W Sigma W^T J^T + 0.3 I for a rotated anisotropic Gaussian and
+    a look-at camera, checked against an independent route: scipy's quaternion
+    rotation and a central-difference Jacobian of the pinhole map."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(13)
+    cam = S.look_at_camera((3.0, -2.0, 1.5), (0.1, 0.2, 0.0), 96, 80, fov_x_deg=50)
+    vm = np.asarray(cam["viewmat"], float)
+    Rv, tv = vm[:, :3], vm[:, 3]
+
+    def proj(X):
+        t = Rv @ X + tv
+        return np.array([cam["fx"] * t[0] / t[2] + cam["cx"], cam["fy"] * t[1] / t[2] + cam["cy"]])
+
+    for _ in range(10):
+        X = rng.uniform(-0.3, 0.3, 3)
+        ls = rng.normal(-2.5, 0.5, 3)
+        q = rng.standard_normal(4)
+        sc = _scene(1, X, ls, quats=q * 1.7)  # unnormalised on purpose
+        p = oracle.preprocess(sc, cam)
+        R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        Sig = R @ np.diag(np.exp(2 * ls)) @ R.T
+        h = 1e-6
+        Jn = np.stack([(proj(X + h * e) - proj(X - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+        Sp = Jn @ Sig @ Jn.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(p["cov2d"][0], [Sp[0, 0], Sp[0, 1], Sp[1, 1]], rtol=1e-7)
+        np.testing.assert_allclose(p["conic"][0].take([0, 1, 1, 2]).reshape(2, 2), np.linalg.inv(Sp), rtol=1e-7)
+        np.testing.assert_allclose(p["mean2d"][0], proj(X), rtol=1e-13)
+
+
+def test_look_at_target_projects_to_principal_point():
+    cam = S.hd_camera(3)
+    sc = _scene(1, [0, 0, 0], [-3] * 3)
+    p = oracle.preprocess(sc, cam)
+    np.testing.assert_allclose(p["mean2d"][0], [960, 540], atol=1e-9)
+
+
+def test_opacity_cull_boundary():
+    """§3.4: a splat with sigma < 1/255 is culled; sigma = 1/255 is kept.
+    sigma < 1/255 <=> logit < -ln 254; the float32 logits on both sides of
+    that value fall on the two sides of the decision."""
+    tau = -math.log(254.0)
+    t32 = np.float32(tau)
+    below = np.nextafter(t32, np.float32(-np.inf)) if float(t32) >= tau else t32
+    above = np.nextafter(t32, np.float32(np.inf)) if float(t32) < tau else t32
+    assert float(below) < tau < float(above)
+    logits = np.array([below, above, -8.0, 0.0], np.float32).astype(float)
+    sc = _scene(4, np.tile([0, 0, 3.0], (4, 1)), np.full((4, 3), -3.0), logits=logits)
+    p = oracle.preprocess(sc, _cam())
+    assert list(p["reason"]) == [1, 0, 1, 0]
+    # exactly at sigma = 1/255 the extent is zero and the centre pixel is kept
+    assert p["extent"][1, 0] < 1e-3
+
+
+def test_near_plane_zero_quaternion_and_offscreen():
+    """Near-plane cull on the float32 depth, a zero quaternion is culled,
+    and a splat whose box misses the viewport by ~1 px is culled while one
+    touching it stays (§3.2 AABB culling)."""
+    f, s = 64.0, 0.02
+    v = (f * s / 2.0) ** 2 + 0.3
+    e = math.sqrt(2 * math.log(255 / (1 + math.exp(-2.0))) * v)
+    x_out = (-1.0 - e - 32) * 2.0 / f      # centre at -1 - e px: box ends 1 px left of 0
+    x_in = (1.0 - e - 32) * 2.0 / f        # box reaches 1 px into the image
+    means = [[0, 0, 0.1], [0, 0, 2.0], [x_out, 0, 2.0], [x_in, 0, 2.0]]
+    quats = [[1, 0, 0, 0], [0, 0, 0, 0], [1, 0, 0, 0], [1, 0, 0, 0]]
+    sc = _scene(4, means, np.full((4, 3), math.log(s)), quats=quats)
+    p = oracle.preprocess(sc, _cam(f=f))
+    assert list(p["reason"]) == [3, 2, 5, 0]
+    assert p["touched"][3] == 2 and list(p["rect"][3]) == [0, 1, 0, 2]
+
+
+def test_tile_corner_touches_four_tiles():
+    """A small splat centred on the corner shared by four 16-px tiles touches
+    exactly those four; one centred in a tile touches one."""
+    sc = _scene(2, [[(16 - 32) / 32.0, (16 - 32) / 32.0, 2.0], [(8 - 32) / 32.0, (8 - 32) / 32.0, 2.0]],
+                np.full((2, 3), math.log(0.02)))
+    p = oracle.preprocess(sc, _cam())
+    assert list(p["touched"]) == [4, 1]
+    assert list(p["rect"][0]) == [0, 0, 1, 1] and list(p["rect"][1]) == [0, 0, 0, 0]
+
+
+def test_depth32_is_float32_evaluation():
+    """The float32 depth with R = I is exactly fl(z + t_z)."""
+    rng = np.random.default_rng(14)
+    vm = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 3]], float)
+    for _ in range(200):
+        X = rng.uniform(-1, 1, 3).astype(np.float32).astype(float)
+        assert oracle.depth32(X, vm) == np.float32(X[2]) + np.float32(3)
+
+
+# ------------------------------------------------------------ blend (§2.1)
+
+def test_single_gaussian_on_pixel_centre():
+    """At the centre of a pixel the splat alpha is min(0.99, sigma):
+    C = c alpha, T = 1 - alpha (E4 with one term)."""
+    for logit in (0.3, 8.0):
+        sc = _scene(1, [(10.5 - 32) / 32.0, (20.5 - 32) / 32.0, 2.0], [math.log(0.03)] * 3, logits=[logit])
+        out = oracle.render(sc, _cam())
+        a = min(0.99, 1 / (1 + math.exp(-logit)))
+        np.testing.assert_allclose(out["image"][20, 10], [a, a, a], rtol=1e-14)
+        np.testing.assert_allclose(out["t_final"][20, 10], 1 - a, rtol=1e-14)
+        assert out["last_gid"][20, 10] == 0
+
+
+def test_stacked_identical_gaussians():
+    """K identical splats at increasing depth but the same projected footprint
+    (scaled with depth): T = (1 - a)^K and C = c (1 - (1 - a)^K)."""
+    K = 7
+    zs = 2.0 + 0.25 * np.arange(K)
+    means = np.stack([np.zeros(K), np.zeros(K), zs], 1) + 0.5 / 64.0 * np.array([1, 1, 0]) * zs[:, None]
+    ls = np.log(0.01 * zs / 2.0)[:, None].repeat(3, 1)
+    sh = np.zeros((K, 16, 3))
+    sh[:, 0, :] = (0.8 - 0.5) / C0
+    sc = _scene(K, means, ls, logits=np.full(K, 0.0), sh=sh)
+    out = oracle.render(sc, _cam())
+    a = 0.5
+    np.testing.assert_allclose(out["t_final"][32, 32], (1 - a) ** K, rtol=1e-12)
+    np.testing.assert_allclose(out["image"][32, 32], 0.8 * (1 - (1 - a) ** K), rtol=1e-12)
+
+
+def test_white_scene_obeys_one_minus_transmittance():
+    """With every colour 1 and a black background, E4 gives C = sum a_i T_i =
+    1 - T_final at every pixel: a dropped term or a wrong transmittance
+    update breaks this."""
+    scene, cam = S.small_forward()
+    sc = dict(scene)
+    sh = np.zeros_like(scene["sh"])
+    sh[:, 0, :] = 0.5 / C0
+    sc["sh"] = sh.astype(np.float32)
+    out = oracle.render(sc, cam)
+    for ch in range(3):
+        np.testing.assert_allclose(out["image"][..., ch], 1 - out["t_final"], atol=1e-12)
+
+
+def test_tile_lists_equal_brute_force_back_to_front():
+    """The per-tile front-to-back result equals a per-pixel back-to-front
+    "over" composite of every visible splat with no tiles (§2.1's order):
+    the opacity-aware extent (§3.4) is conservative, so tiles lose nothing."""
+    scene = S.uniform_scene(400, seed=21)
+    cam = {"viewmat": np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 3]], np.float32),
+           "fx": 40.0, "fy": 40.0, "cx": 24.0, "cy": 20.0, "width": 48, "height": 40,
+           "znear": 0.2, "bg": (0.1, 0.2, 0.3)}
+    for tile in (8, 16):
+        out = oracle.render(scene, cam, tile=tile)
+        img, tf = oracle.blend_brute(cam, out["proj"])
+        ok = out["n_amb"] == 0
+        assert ok.mean() > 0.99
+        np.testing.assert_allclose(out["image"][ok], img[ok], atol=1e-12)
+        np.testing.assert_allclose(out["t_final"][ok], tf[ok], atol=1e-12)
+
+
+# ------------------------------------------------------------- sort (§3.3)
+
+@pytest.mark.parametrize("n", [0, 1, 31, 4097, 100_000])
+@pytest.mark.parametrize("kind", ["random", "equal", "sorted", "reversed", "few"])
+def test_sort_is_stable_sort(n, kind):
+    """§3.3.2: equal keys keep their input order. Matches numpy's stable
+    argsort (a library special case) on every input shape."""
+    rng = np.random.default_rng(n + len(kind))
+    if kind == "random":
+        keys = rng.integers(0, 2 ** 45, n, dtype=np.uint64)
+    elif kind == "equal":
+        keys = np.full(n, 12345, np.uint64)
+    elif kind == "sorted":
+        keys = np.sort(rng.integers(0, 2 ** 40, n, dtype=np.uint64))
+    elif kind == "reversed":
+        keys = np.sort(rng.integers(0, 2 ** 40, n, dtype=np.uint64))[::-1].copy()
+    else:
+        keys = rng.integers(0, 3, n).astype(np.uint64) << np.uint64(33)
+    vals = np.arange(n, dtype=np.uint32)
+    k, v = oracle.sort_pairs(keys, vals)
+    perm = np.argsort(keys, kind="stable")
+    np.testing.assert_array_equal(k, keys[perm])
+    np.testing.assert_array_equal(v, vals[perm])
+
+
+def test_emission_and_ranges():
+    """Key emission: Gaussian i emits touched_i keys in row-major tile order,
+    offsets are their exclusive scan; tile ranges equal searchsorted bounds."""
+    scene, cam = S.small_forward()
+    out = oracle.render(scene, cam)
+    p = out["proj"]
+    np.testing.assert_array_equal(np.diff(out["offsets"]), p["touched"])
+    keys, vals = out["keys"], out["vals"]
+    np.testing.assert_array_equal(np.bincount(vals, minlength=p["touched"].size), p["touched"])
+    assert np.all((keys & np.uint64(0x7FFFFFFF)) == p["depth"][vals].view(np.uint32))
+    tx = (cam["width"] + 15) // 16
+    tiles = (keys >> np.uint64(31)).astype(np.int64)
+    i = 123
+    r = p["rect"][i]
+    got = tiles[out["offsets"][i]:out["offsets"][i + 1]]
+    exp = [ty * tx + x for ty in range(r[1], r[3] + 1) for x in range(r[0], r[2] + 1)]
+    assert list(got) == exp
+    sk = out["sorted_keys"]
+    st = (sk >> np.uint64(31)).astype(np.int64)
+    rng_ = out["ranges"]
+    for t in range(0, tx * tx, 7):
+        lo, hi = np.searchsorted(st, t, "left"), np.searchsorted(st, t, "right")
+        if hi > lo:
+            assert (rng_[t] == [lo, hi]).all()
+
+
+# ----------------------------------------------------------- gradient (§1)
+
+@pytest.mark.parametrize("big", [False, True])
+def test_gradient_matches_central_differences(big):
+    """The oracle's analytic FP64 gradient of L = 1/2 ||C - target||^2 agrees
+    with FP64 central differences on 64 Gaussians at 32x32 (entries whose
+    step changes a discrete decision are skipped and counted). The second
+    scene uses larger, overlapping splats so occlusion terms matter."""
+    scene, cam, target = S.gradcheck_scene()
+    if big:
+        scene = S.uniform_scene(64, seed=7, log_scale_mean=-2.3, log_scale_std=0.3)
+    sc = {k: v.astype(np.float64) for k, v in scene.items()}
+    base = oracle.loss_grad(sc, cam, target)
+    h = 1e-6
+    skipped = checked = 0
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        flat = sc[name].reshape(-1)
+        g = base["grads"][name].reshape(-1)
+        fd = np.zeros_like(g)
+        mask = np.zeros(g.size, bool)
+        for j in range(flat.size):
+            old = flat[j]
+            flat[j] = old + h
+            p = oracle.loss_grad(sc, cam, target, grads=False)
+            flat[j] = old - h
+            m = oracle.loss_grad(sc, cam, target, grads=False)
+            flat[j] = old
+            if p["fingerprint"] != base["fingerprint"] or m["fingerprint"] != base["fingerprint"]:
+                skipped += 1
+                continue
+            fd[j] = (p["loss"] - m["loss"]) / (2 * h)
+            mask[j] = True
+        checked += mask.sum()
+        err = np.linalg.norm(g[mask] - fd[mask]) / max(np.linalg.norm(fd[mask]), 1e-12)
+        assert err < 1e-6, (name, err)
+        # sanity: gradients are non-trivial
+        assert np.linalg.norm(g[mask]) > 0, name
+    assert skipped < 0.02 * (checked + skipped)
