@@ -1,0 +1,221 @@
+/*
+ * websplat.h -- C ABI of the GB300 (sm_103a) 3D Gaussian Splatting render
+ * path studied in "WebSplatter" (arXiv 2602.03207).
+ *
+ * A frame is four calls on one CUDA stream, in this order:
+ *   ws_preprocess  -> ws_cull -> ws_sort -> ws_rasterize
+ * and, for training, ws_rasterize_backward after ws_rasterize.
+ *
+ * Conventions shared by every entry point
+ *   - The caller owns all memory. The library never allocates or frees
+ *     device memory; scratch lives in a caller-provided workspace of
+ *     ws_workspace_bytes() bytes. Every pointer argument named "device" is
+ *     a CUDA device pointer; every struct pointer is a host pointer read
+ *     before the call returns.
+ *   - Device pointers must be 16-byte aligned (vector loads); a misaligned
+ *     pointer returns WS_ERR_INVALID_ARG.
+ *   - All work is enqueued asynchronously on `stream` (a cudaStream_t; NULL
+ *     is the legacy default stream). No call synchronises the host, so a
+ *     whole frame can be captured into a CUDA graph.
+ *   - Argument errors are detected on the host before any launch and
+ *     returned synchronously (WS_ERR_INVALID_ARG / WS_ERR_UNSUPPORTED); a
+ *     launch failure returns WS_ERR_CUDA. Data-dependent errors (more keys
+ *     than key_capacity) are recorded in a status word inside the workspace
+ *     and read with ws_read_status() after the stream has been synchronised.
+ *   - n = 0 and an empty key list are valid; the image is then the
+ *     background colour.
+ *
+ * Layouts (all float32, C-contiguous, Gaussian-major):
+ *   means[n][3] world position; log_scales[n][3] log of the per-axis
+ *   standard deviations; quats[n][4] rotation quaternion (w, x, y, z), any
+ *   non-zero norm; opacity_logits[n]; sh[n][16][3] degree-3 spherical
+ *   harmonic coefficients, coefficient-major (index l*l + l + m, real SH
+ *   with the Condon-Shortley phase, i.e. the 3DGS PLY convention).
+ */
+#ifndef WEBSPLAT_H
+#define WEBSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ws_status;
+#define WS_OK 0
+#define WS_ERR_INVALID_ARG 1
+#define WS_ERR_CUDA 2
+#define WS_ERR_CAPACITY 3
+#define WS_ERR_TIMEOUT 4
+#define WS_ERR_UNSUPPORTED 5
+
+#define WS_ABI_VERSION 1
+
+/* Status bits written to the device status word. */
+#define WS_FLAG_CAPACITY 1u /* more (tile, splat) pairs than key_capacity */
+#define WS_FLAG_TIMEOUT 2u  /* a bounded wait ran out (look-back sort only) */
+
+/* Pinhole camera (§3.2 projects each centre and covariance to the image).
+ * viewmat: row-major 3x4 [R | t] world -> camera, OpenCV axes (x right,
+ * y down, z forward). Pixel u covers [u, u+1), so its centre is u + 1/2.
+ * Splats with float32 view depth <= znear are culled. bg: background RGB. */
+typedef struct ws_camera {
+    float viewmat[12];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear;
+    float bg[3];
+} ws_camera;
+
+/* Frame configuration.
+ *   tile        tile side in pixels: 8, 16 or 32
+ *   digit_bits  radix-sort digit width: 4..8 (ws_sort)
+ *   dilation    px^2 added to the diagonal of the projected covariance (0.3)
+ *   guard       frustum guard factor of the EWA Jacobian clamp (1.3)
+ *   flags       WS_CFG_* bits below                                        */
+typedef struct ws_config {
+    int32_t tile;
+    int32_t digit_bits;
+    float dilation;
+    float guard;
+    uint32_t flags;
+} ws_config;
+
+#define WS_CFG_NO_OPACITY_CULL 1u /* ablation: keep splats with sigma < 1/255 */
+#define WS_CFG_NO_AABB_CULL 2u    /* ablation: keep splats whose box misses the viewport */
+
+/* Library ABI version (WS_ABI_VERSION of the build). */
+int32_t ws_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *ws_status_string(ws_status s);
+
+/* Bytes of workspace the calls below need for n Gaussians, at most
+ * key_capacity (tile, splat) pairs, this camera's tile grid and this
+ * configuration. Returns 0 for invalid arguments. */
+size_t ws_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera *cam,
+                          const ws_config *cfg);
+
+/* Pre-processing stage (§3.2, with §2.1's covariance and colour and §3.4's
+ * opacity culling and opacity-aware extent). One thread per Gaussian:
+ *   sigma = 1/(1+exp(-logit)); culled if sigma < 1/255 (decided exactly as
+ *   logit < -ln 254), if the quaternion is zero, or if the float32 view
+ *   depth ((r20 x + r21 y) + r22 z) + t2, evaluated with each operation
+ *   rounded, is <= znear;
+ *   Sigma = R(q) diag(exp(2 log_scale)) R(q)^T; Sigma' = J W Sigma W^T J^T
+ *   + dilation I with the EWA Jacobian J (t_x/t_z, t_y/t_z clamped to the
+ *   guard band inside J); conic = Sigma'^{-1};
+ *   extent e = sqrt(2 ln(255 sigma) diag(Sigma')) -- the box of the ellipse
+ *   where sigma exp(-q/2) >= 1/255 (§3.4's cutoff, read with r^2 = q/2);
+ *   culled if [m - e, m + e] misses [0, W) x [0, H) (§3.2 AABB culling);
+ *   rgb = max(0, sum_lm sh_lm Y_lm(d) + 1/2), d = normalise(X - camera).
+ * Inputs: the Gaussian arrays (device, layouts above).
+ * Outputs (device, caller-allocated, n entries each):
+ *   mean2d[n][4]  projected centre as the unevaluated double-float sum
+ *                 (x_hi + x_lo, y_hi + y_lo), stored (x_hi, y_hi, x_lo, y_lo);
+ *                 x_hi alone is the float32-rounded centre
+ *   conic[n][3]   (a, b, c) of Sigma'^{-1} = [[a, b], [b, c]]
+ *   depth[n]      float32 view depth (written for every Gaussian)
+ *   rgb[n][3], opacity[n] (sigma)
+ *   rect[n][4]    uint16 tile rectangle x0, y0, x1, y1 (inclusive)
+ *   tiles_touched[n]  uint32 tiles in rect; 0 means culled
+ * For a culled Gaussian only depth and tiles_touched are written. */
+ws_status ws_preprocess(int64_t n, const float *means, const float *log_scales,
+                        const float *quats, const float *opacity_logits, const float *sh,
+                        const ws_camera *cam, const ws_config *cfg,
+                        float *mean2d, float *conic, float *depth, float *rgb, float *opacity,
+                        uint16_t *rect, uint32_t *tiles_touched, void *stream);
+
+/* Compaction of the surviving splats into the <tile, splat> pair list
+ * (§3.2: "the alive primitives are written into a buffer"; §3.4 describes
+ * the tile-based pair list this path uses). A wait-free two-level scan
+ * (one dispatch per level, no inter-block waiting, no global atomics) of
+ * tiles_touched gives
+ *   offsets[i] = sum_{j<i} tiles_touched[j]   (device, n + 1 entries,
+ *                offsets[n] = total pairs),
+ * and every visible Gaussian i writes, for each tile (tx, ty) of its rect in
+ * row-major order, at slot offsets[i] + k:
+ *   keys[slot] = ((ty * tiles_x + tx) << 31) | float32 bits of depth[i]
+ *   vals[slot] = i
+ * (the depth is positive, so its sign bit is 0 and key order is (tile,
+ * depth) order). num_keys (device, one uint32) receives min(total,
+ * key_capacity); pairs past key_capacity are dropped and WS_FLAG_CAPACITY
+ * is raised. Clears the workspace status word first. key_capacity must be
+ * < 2^31. */
+ws_status ws_cull(int64_t n, const uint32_t *tiles_touched, const uint16_t *rect,
+                  const float *depth, const ws_camera *cam, const ws_config *cfg,
+                  uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t key_capacity,
+                  uint32_t *num_keys, void *workspace, void *stream);
+
+/* Stable LSD radix sort of (keys, vals) by key bits [begin_bit, end_bit)
+ * (§3.3.2). Each pass of cfg->digit_bits bits is three dispatches:
+ * per-block digit histograms, a scan of the digit-major histogram matrix
+ * giving base_d + prefix_wg for every (digit, block), and a stable scatter
+ * to pos = base_d + prefix_wg + rank_local. No block ever waits for
+ * another and there are no global atomics, so the result does not depend
+ * on scheduling. The key count is read from num_keys (device) so the
+ * launch needs no host synchronisation; key_capacity bounds the grids.
+ * keys_alt / vals_alt (device, key_capacity entries) are the ping-pong
+ * buffers. *result_in_alt (host) is set to 1 when the sorted data ends in
+ * the _alt buffers (odd pass count), else 0. begin_bit < end_bit <= 64. */
+ws_status ws_sort(const uint32_t *num_keys, int64_t key_capacity, int32_t begin_bit,
+                  int32_t end_bit, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                  uint32_t *vals_alt, const ws_config *cfg, void *workspace,
+                  int32_t *result_in_alt, void *stream);
+
+/* Rasterisation stage (§3.4 with §2.1's compositing), per 16x16 (tile^2)
+ * pixel tile, front to back over the tile's depth-sorted list:
+ *   a = min(0.99, sigma exp(-q/2)), q = d^T conic d, d = pixel centre -
+ *   centre; pairs with a < 1/255 are skipped; C += rgb a T; T *= 1 - a;
+ *   image = C + T bg.
+ * Inputs: num_keys (device), sorted keys and vals (device), the
+ * ws_preprocess outputs. Outputs (device): ranges[tiles][2] uint32 [start,
+ * end) of every tile in the sorted list; image[H][W][3]; t_final[H][W]
+ * (final transmittance); n_contrib[H][W] (1 + list position, relative to
+ * the tile's start, of the last splat composited; 0 if none). */
+ws_status ws_rasterize(const uint32_t *num_keys, const uint64_t *keys, const uint32_t *vals,
+                       const float *mean2d, const float *conic, const float *opacity,
+                       const float *rgb, const ws_camera *cam, const ws_config *cfg,
+                       uint32_t *ranges, float *image, float *t_final, uint32_t *n_contrib,
+                       void *stream);
+
+/* Backward of the whole frame for a loss L(image): given d_image = dL/dimage
+ * (device, [H][W][3]), writes dL/d(means, log_scales, quats, opacity_logits,
+ * sh) (device, the input layouts; zero for culled Gaussians). The paper has
+ * no backward (§1 only notes that the representation is differentiable);
+ * this is the adjoint of the forward defined above, with no gradient
+ * through the 0.99 alpha clamp, the Jacobian's guard-band clamp or a colour
+ * channel clamped at 0.
+ * Deterministic, without float atomics: each tile walks its list back to
+ * front from t_final / n_contrib, reduces each pair's 9 partial derivatives
+ * (centre 2, conic 3, sigma 1, colour 3) inside the block in a fixed order
+ * and writes them to the pair's emission slot offsets[g] + k in the
+ * workspace; each Gaussian then sums its slots in order and applies the
+ * adjoint of its pre-processing. Bitwise reproducible.
+ * Inputs: the Gaussians and camera/config of the forward, the ws_preprocess
+ * outputs, offsets (ws_cull), the sorted vals (ws_sort), ranges, t_final and
+ * n_contrib (ws_rasterize) of the SAME frame, and the key_capacity the
+ * workspace was sized with. opacity_logits may be NULL (sigma is read from
+ * `opacity`). */
+ws_status ws_rasterize_backward(int64_t n, const float *means, const float *log_scales,
+                                const float *quats, const float *opacity_logits, const float *sh,
+                                const ws_camera *cam, const ws_config *cfg, const float *mean2d,
+                                const float *conic, const float *rgb, const float *opacity,
+                                const uint16_t *rect, const uint32_t *offsets,
+                                const uint32_t *tiles_touched, const uint32_t *vals,
+                                const uint32_t *ranges, const float *t_final, const uint32_t *n_contrib,
+                                const float *d_image, int64_t key_capacity, float *d_means,
+                                float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                                float *d_sh, void *workspace, void *stream);
+
+/* Reads (and, if clear != 0, clears) the device status word of a workspace:
+ * waits for `stream`, then stores the WS_FLAG_* bits in *flags (host). This
+ * is the one call that synchronises the host. */
+ws_status ws_read_status(void *workspace, uint32_t *flags, int32_t clear, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WEBSPLAT_H */

@@ -1,0 +1,236 @@
+// extern "C" entry points of websplat.h: host-side argument checks, frame
+// constants and workspace layout; every launch goes to the kernels in
+// ws_preprocess.cu, ws_cull.cu, ws_sort.cu and ws_raster.cu.
+#include <cmath>
+#include <cstring>
+
+#include "websplat.h"
+#include "ws_common.cuh"
+#include "ws_kernels.cuh"
+
+namespace {
+
+using ws::Frame;
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool valid_tile(int t) { return t == 8 || t == 16 || t == 32; }
+
+bool valid_camera(const ws_camera* c) {
+    if (!c) return false;
+    if (c->width <= 0 || c->height <= 0 || c->width > 65535 * 8 || c->height > 65535 * 8) return false;
+    if (!(c->fx > 0.f) || !(c->fy > 0.f) || !(c->znear >= 0.f)) return false;
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(c->viewmat[i])) return false;
+    return std::isfinite(c->cx) && std::isfinite(c->cy);
+}
+
+bool valid_config(const ws_config* g) {
+    return g && valid_tile(g->tile) && g->dilation >= 0.f && g->guard > 0.f;
+}
+
+Frame make_frame(const ws_camera* c, const ws_config* g) {
+    Frame f;
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) f.R[3 * r + k] = c->viewmat[4 * r + k];
+        f.t[r] = c->viewmat[4 * r + 3];
+    }
+    for (int k = 0; k < 3; ++k)
+        f.campos[k] = -(f.R[k] * f.t[0] + f.R[3 + k] * f.t[1] + f.R[6 + k] * f.t[2]);
+    f.fx = c->fx;
+    f.fy = c->fy;
+    f.cx = c->cx;
+    f.cy = c->cy;
+    f.znear = c->znear;
+    f.limx = g->guard * 0.5f * (float)c->width / c->fx;
+    f.limy = g->guard * 0.5f * (float)c->height / c->fy;
+    f.dilation = g->dilation;
+    for (int k = 0; k < 3; ++k) f.bg[k] = c->bg[k];
+    f.W = c->width;
+    f.H = c->height;
+    f.TS = g->tile;
+    f.TX = (c->width + g->tile - 1) / g->tile;
+    f.TY = (c->height + g->tile - 1) / g->tile;
+    f.flags = g->flags;
+    return f;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Workspace layout: [status | sort scratch | pair records | compaction
+// scratch]. The first three depend only on the key capacity (the sort region
+// is sized for the widest supported digit, so any digit width fits), so
+// ws_sort and ws_rasterize_backward find their regions without knowing n.
+constexpr int kMaxDigitBits = 8;
+
+struct Layout {
+    size_t status, sort, bwd, cull, total;
+};
+
+Layout layout(int64_t n, int64_t cap) {
+    Layout L;
+    L.status = 0;
+    L.sort = align_up(ws::kStatusBytes);
+    L.bwd = L.sort + align_up(ws::sort_scratch_bytes(cap, kMaxDigitBits));
+    L.cull = L.bwd + align_up(ws::backward_scratch_bytes(cap));
+    L.total = L.cull + align_up(ws::cull_scratch_bytes(n));
+    return L;
+}
+
+ws_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WS_OK : WS_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int32_t ws_abi_version(void) { return WS_ABI_VERSION; }
+
+const char* ws_status_string(ws_status s) {
+    switch (s) {
+        case WS_OK: return "ok";
+        case WS_ERR_INVALID_ARG: return "invalid argument";
+        case WS_ERR_CUDA: return "CUDA error";
+        case WS_ERR_CAPACITY: return "key capacity exceeded";
+        case WS_ERR_TIMEOUT: return "bounded wait timed out";
+        case WS_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+size_t ws_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera* cam, const ws_config* cfg) {
+    if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 31)) return 0;
+    if (!valid_camera(cam) || !valid_config(cfg) || !ws::sort_digit_supported(cfg->digit_bits)) return 0;
+    return layout(n, key_capacity).total;
+}
+
+ws_status ws_preprocess(int64_t n, const float* means, const float* log_scales, const float* quats,
+                        const float* opacity_logits, const float* sh, const ws_camera* cam,
+                        const ws_config* cfg, float* mean2d, float* conic, float* depth, float* rgb,
+                        float* opacity, uint16_t* rect, uint32_t* tiles_touched, void* stream) {
+    if (n < 0 || n >= (int64_t(1) << 32) || !valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
+    if (n == 0) return WS_OK;
+    const void* ptrs[] = {means, log_scales, quats, opacity_logits, sh, mean2d, conic, depth,
+                          rgb, opacity, rect, tiles_touched};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    const Frame f = make_frame(cam, cfg);
+    if (f.TX > 65535 || f.TY > 65535) return WS_ERR_UNSUPPORTED;
+    return cuda_status(ws::launch_preprocess(n, means, log_scales, quats, opacity_logits, sh, f,
+                                             mean2d, conic, depth, rgb, opacity, rect, tiles_touched,
+                                             static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_cull(int64_t n, const uint32_t* tiles_touched, const uint16_t* rect, const float* depth,
+                  const ws_camera* cam, const ws_config* cfg, uint32_t* offsets, uint64_t* keys,
+                  uint32_t* vals, int64_t key_capacity, uint32_t* num_keys, void* workspace,
+                  void* stream) {
+    if (n < 0 || n >= (int64_t(1) << 32) || key_capacity < 0 || key_capacity >= (int64_t(1) << 31))
+        return WS_ERR_INVALID_ARG;
+    if (!valid_camera(cam) || !valid_config(cfg) || !ws::sort_digit_supported(cfg->digit_bits))
+        return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {offsets, num_keys, workspace};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (n > 0) {
+        const void* in[] = {tiles_touched, rect, depth};
+        for (const void* p : in)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    if (key_capacity > 0 && (!keys || !vals || !aligned16(keys) || !aligned16(vals))) return WS_ERR_INVALID_ARG;
+    const Frame f = make_frame(cam, cfg);
+    const Layout L = layout(n, key_capacity);
+    char* ws_base = static_cast<char*>(workspace);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws_base + L.status);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(status, 0, ws::kStatusBytes, s);
+    if (e != cudaSuccess) return WS_ERR_CUDA;
+    return cuda_status(ws::launch_cull(n, tiles_touched, rect, depth, f, offsets, keys, vals,
+                                       key_capacity, num_keys, status, ws_base + L.cull, s));
+}
+
+ws_status ws_sort(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_bit, int32_t end_bit,
+                  uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                  const ws_config* cfg, void* workspace, int32_t* result_in_alt, void* stream) {
+    if (!cfg || !ws::sort_digit_supported(cfg->digit_bits)) return WS_ERR_UNSUPPORTED;
+    if (key_capacity < 0 || key_capacity >= (int64_t(1) << 31) || begin_bit < 0 || end_bit > 64 ||
+        begin_bit >= end_bit || !result_in_alt)
+        return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, workspace};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (key_capacity > 0) {
+        const void* kp[] = {keys, vals, keys_alt, vals_alt};
+        for (const void* p : kp)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    char* ws_base = static_cast<char*>(workspace);
+    int in_alt = 0;
+    cudaError_t e = ws::launch_sort(num_keys, key_capacity, begin_bit, end_bit, cfg->digit_bits, keys,
+                                    vals, keys_alt, vals_alt, ws_base + layout(0, key_capacity).sort,
+                                    &in_alt, static_cast<cudaStream_t>(stream));
+    *result_in_alt = in_alt;
+    return cuda_status(e);
+}
+
+ws_status ws_rasterize(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals,
+                       const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                       const ws_camera* cam, const ws_config* cfg, uint32_t* ranges, float* image,
+                       float* t_final, uint32_t* n_contrib, void* stream) {
+    if (!valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, keys, vals, mean2d, conic, opacity, rgb, ranges, image, t_final, n_contrib};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    const Frame f = make_frame(cam, cfg);
+    return cuda_status(ws::launch_rasterize(num_keys, 0, keys, vals, mean2d, conic, opacity, rgb, f, ranges,
+                                            image, t_final, n_contrib, static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_rasterize_backward(int64_t n, const float* means, const float* log_scales,
+                                const float* quats, const float* opacity_logits, const float* sh,
+                                const ws_camera* cam, const ws_config* cfg, const float* mean2d,
+                                const float* conic, const float* rgb, const float* opacity,
+                                const uint16_t* rect, const uint32_t* offsets,
+                                const uint32_t* tiles_touched, const uint32_t* vals,
+                                const uint32_t* ranges, const float* t_final, const uint32_t* n_contrib,
+                                const float* d_image, int64_t key_capacity, float* d_means,
+                                float* d_log_scales, float* d_quats, float* d_opacity_logits,
+                                float* d_sh, void* workspace, void* stream) {
+    (void)opacity_logits;  // sigma is read back from `opacity`
+    if (n < 0 || n >= (int64_t(1) << 32) || key_capacity < 0 || key_capacity >= (int64_t(1) << 31))
+        return WS_ERR_INVALID_ARG;
+    if (!valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {ranges, t_final, n_contrib, d_image, workspace, offsets};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (n > 0) {
+        const void* per[] = {means, log_scales, quats, sh, mean2d, conic, rgb, opacity, rect,
+                             tiles_touched, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
+        for (const void* p : per)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    if (key_capacity > 0 && (!vals || !aligned16(vals))) return WS_ERR_INVALID_ARG;
+    const Frame f = make_frame(cam, cfg);
+    char* ws_base = static_cast<char*>(workspace);
+    return cuda_status(ws::launch_backward(n, means, log_scales, quats, sh, f, mean2d, conic, rgb, opacity,
+                                           rect, offsets, tiles_touched, vals, ranges, t_final, n_contrib,
+                                           d_image, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
+                                           ws_base + layout(0, key_capacity).bwd,
+                                           static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_read_status(void* workspace, uint32_t* flags, int32_t clear, void* stream) {
+    if (!workspace || !flags || !aligned16(workspace)) return WS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t words[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(words, workspace, sizeof(words), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return WS_ERR_CUDA;
+    *flags = (words[0] ? WS_FLAG_CAPACITY : 0u) | (words[1] ? WS_FLAG_TIMEOUT : 0u);
+    if (clear) {
+        e = cudaMemsetAsync(workspace, 0, ws::kStatusBytes, s);
+        if (e != cudaSuccess) return WS_ERR_CUDA;
+    }
+    return WS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Device helpers shared by the render-path kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "websplat.h"
+
+namespace ws {
+
+constexpr int kWarp = 32;
+constexpr uint32_t kFull = 0xffffffffu;
+
+// Bytes reserved at the head of every workspace for the status words.
+constexpr size_t kStatusBytes = 256;
+
+// Camera and frame constants, derived on the host once per call and passed
+// by value to every kernel.
+struct Frame {
+    float R[9];       // world -> camera rotation, row-major
+    float t[3];       // world -> camera translation
+    float campos[3];  // camera centre in world coordinates (-R^T t)
+    float fx, fy, cx, cy;
+    float znear;
+    float limx, limy; // guard-band limits of t_x/t_z and t_y/t_z inside J
+    float dilation;
+    float bg[3];
+    int W, H;
+    int TS, TX, TY;   // tile side and tile grid
+    uint32_t flags;
+};
+
+// ---------------------------------------------------------------------------
+// Double-float ("unevaluated sum of two floats") arithmetic. Error-free
+// transformations of Knuth (two-sum) and Dekker (two-product via a fused
+// multiply-add); intrinsics keep the compiler from contracting or
+// reassociating them.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+
+// r0*x + r1*y + r2*z + t in double-float (inputs exact floats).
+__device__ __forceinline__ DF df_affine3(float r0, float r1, float r2, float x, float y, float z,
+                                         float t) {
+    DF acc = {t, 0.f};
+    DF p = two_prod(r0, x);
+    DF s = two_sum(acc.hi, p.hi);
+    float lo = __fadd_rn(p.lo, s.lo);
+    acc.hi = s.hi;
+    p = two_prod(r1, y);
+    s = two_sum(acc.hi, p.hi);
+    lo = __fadd_rn(lo, __fadd_rn(p.lo, s.lo));
+    acc.hi = s.hi;
+    p = two_prod(r2, z);
+    s = two_sum(acc.hi, p.hi);
+    lo = __fadd_rn(lo, __fadd_rn(p.lo, s.lo));
+    return quick_two_sum(s.hi, lo);
+}
+
+// a / b for double-float a, b (one Newton-style correction step).
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    DF p = two_prod(q1, b.hi);
+    float r = __fsub_rn(__fsub_rn(a.hi, p.hi), p.lo);
+    r = __fadd_rn(r, a.lo);
+    r = __fsub_rn(r, __fmul_rn(q1, b.lo));
+    float q2 = __fdiv_rn(r, b.hi);
+    return quick_two_sum(q1, q2);
+}
+
+// f * u + c for float f, c and double-float u.
+__device__ __forceinline__ DF df_scale_add(float f, DF u, float c) {
+    DF p = two_prod(f, u.hi);
+    float plo = __fmaf_rn(f, u.lo, p.lo);
+    DF s = two_sum(p.hi, c);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, plo));
+}
+
+// ---------------------------------------------------------------------------
+// 2^x on the special-function unit (the PTX ex2.approx instruction).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kAlphaMin = 1.0f / 255.0f;  // §3.4 quantisation threshold
+constexpr float kAlphaMax = 0.99f;
+// ln(255): the extent threshold is q_c = 2 (ln 255 + ln sigma).
+constexpr float kLn255 = 5.541263545158426f;
+// sigma < 1/255  <=>  logit < -ln(254)
+constexpr double kOpacityLogitMin = -5.537334267018537;
+
+// Splat alpha at a pixel, from tile-relative offsets and the conic
+// premultiplied by -log2(e)/2 (A, C) and -log2(e) (B):
+//   a = min(0.99, sigma 2^(A dx^2 + B dx dy + C dy^2)).
+// The forward and the backward both call this, so they take the same
+// 1/255 decision bit for bit.
+__device__ __forceinline__ float splat_power2(float dx, float dy, float A, float B, float C) {
+    float u = __fmaf_rn(A, dx, __fmul_rn(B, dy));
+    return __fmaf_rn(dx, u, __fmul_rn(__fmul_rn(C, dy), dy));
+}
+
+__device__ __forceinline__ float splat_alpha(float dx, float dy, float A, float B, float C,
+                                             float opacity) {
+    return fminf(kAlphaMax, __fmul_rn(opacity, ex2_approx(splat_power2(dx, dy, A, B, C))));
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one uint32 per thread (THREADS threads).
+// `smem` must hold THREADS / 32 + 1 words. Returns the exclusive prefix and
+// writes the block total to *total.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* smem,
+                                                         uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = THREADS / 32;
+        uint32_t w = lane < NW ? smem[lane] : 0u;
+        uint32_t s = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < NW) smem[lane] = s - w;
+        if (lane == NW - 1) smem[NW] = s;
+    }
+    __syncthreads();
+    uint32_t r = smem[warp] + x - v;
+    *total = smem[THREADS / 32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void set_flag(uint32_t* status, uint32_t bit) {
+    // A plain store of a fixed value: every writer stores the same bit to
+    // its own word, so no read-modify-write is needed.
+    status[bit == WS_FLAG_CAPACITY ? 0 : 1] = 1u;
+}
+
+}  // namespace ws

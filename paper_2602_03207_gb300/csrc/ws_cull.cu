@@ -1,0 +1,155 @@
+// Compaction of the surviving splats into the <tile, splat> pair list.
+//
+// §3.2 writes the "alive primitives" into a buffer; this path writes one
+// (tile, depth) key per overlapped tile (the tile decomposition §3.4
+// describes). The slot of every pair comes from an exclusive scan of
+// tiles_touched, computed wait-free in the spirit of §3.3.2's hierarchical
+// scan: level 0 reduces fixed chunks, level 1 scans the chunk sums in one
+// block, and level 0 again scans inside each chunk and adds its chunk
+// offset. Three dispatches, no block waits for another, no global atomics.
+//
+// Emission is balanced over pairs rather than over Gaussians: a block owns a
+// chunk of Gaussians and the contiguous slot range their pairs occupy; its
+// threads walk that slot range in order, so every key/value write is
+// coalesced no matter how many tiles one splat covers. A thread finds the
+// Gaussian of its slot by binary search over the chunk's local offsets in
+// shared memory.
+#include "ws_common.cuh"
+#include "ws_kernels.cuh"
+
+namespace ws {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kChunk = kScanThreads * kScanItems;  // Gaussians per block
+constexpr int kTopThreads = 1024;
+
+// Level 0 up: one sum of tiles_touched per chunk.
+__global__ void __launch_bounds__(kScanThreads)
+k_chunk_sums(int64_t n, const uint32_t* __restrict__ touched, uint32_t* __restrict__ sums) {
+    __shared__ uint32_t s_red[kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + threadIdx.x + k * kScanThreads;
+        if (i < n) acc += __ldg(touched + i);
+    }
+    uint32_t total;
+    block_exclusive_scan<kScanThreads>(acc, s_red, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Level 1: exclusive scan of the chunk sums in one block; total pairs,
+// the clamped key count and the capacity flag.
+__global__ void __launch_bounds__(kTopThreads)
+k_chunk_scan(int64_t nchunks, int64_t n, uint32_t* __restrict__ sums, uint32_t* __restrict__ offsets,
+             uint32_t* __restrict__ num_keys, int64_t capacity, uint32_t* __restrict__ status) {
+    __shared__ uint32_t s_red[kTopThreads / 32 + 1];
+    uint32_t carry = 0;
+    for (int64_t start = 0; start < nchunks; start += kTopThreads) {
+        int64_t c = start + threadIdx.x;
+        uint32_t v = c < nchunks ? sums[c] : 0u;
+        uint32_t total;
+        uint32_t ex = block_exclusive_scan<kTopThreads>(v, s_red, &total);
+        if (c < nchunks) sums[c] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        offsets[n] = carry;
+        uint32_t k = (int64_t)carry > capacity ? (uint32_t)capacity : carry;
+        *num_keys = k;
+        if ((int64_t)carry > capacity) set_flag(status, WS_FLAG_CAPACITY);
+    }
+}
+
+// Level 0 down + emission.
+__global__ void __launch_bounds__(kScanThreads)
+k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
+       const float* __restrict__ depth, const uint32_t* __restrict__ chunk_off, int tiles_x,
+       uint32_t* __restrict__ offsets, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+       int64_t capacity) {
+    __shared__ uint32_t s_off[kChunk + 1];
+    __shared__ uint2 s_rect[kChunk];
+    __shared__ uint32_t s_depth[kChunk];
+    __shared__ uint32_t s_red[kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    const int cnt = (int)((n - base) < kChunk ? (n - base) : kChunk);
+
+    // Blocked arrangement: thread t owns Gaussians base + t*8 .. base + t*8 + 7,
+    // so a thread-serial prefix plus one block scan gives the local offsets.
+    uint32_t v[kScanItems];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int li = threadIdx.x * kScanItems + k;
+        v[k] = li < cnt ? __ldg(touched + base + li) : 0u;
+        acc += v[k];
+    }
+    uint32_t total;
+    uint32_t ex = block_exclusive_scan<kScanThreads>(acc, s_red, &total);
+    const uint32_t coff = chunk_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int li = threadIdx.x * kScanItems + k;
+        s_off[li] = ex;
+        if (li < cnt) offsets[base + li] = coff + ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) s_off[kChunk] = total;
+    // Stage rect and depth of the chunk (coalesced).
+    for (int li = threadIdx.x; li < cnt; li += kScanThreads) {
+        s_rect[li] = __ldg(rect + base + li);
+        s_depth[li] = __float_as_uint(__ldg(depth + base + li));
+    }
+    __syncthreads();
+
+    // Walk the chunk's slot range; slot -> Gaussian by binary search.
+    for (uint32_t s = threadIdx.x; s < total; s += kScanThreads) {
+        int64_t slot = (int64_t)coff + s;
+        if (slot >= capacity) break;
+        int lo = 0, hi = cnt - 1;  // largest g with s_off[g] <= s
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= s) lo = mid; else hi = mid - 1;
+        }
+        uint32_t j = s - s_off[lo];
+        uint2 r = s_rect[lo];
+        uint32_t rx0 = r.x & 0xffffu, ry0 = r.x >> 16, rx1 = r.y & 0xffffu;
+        uint32_t w = rx1 - rx0 + 1;
+        uint32_t dy = j / w, dx = j - dy * w;
+        uint64_t tile = (uint64_t)(ry0 + dy) * (uint64_t)tiles_x + (rx0 + dx);
+        keys[slot] = (tile << 31) | (uint64_t)(s_depth[lo] & 0x7fffffffu);
+        vals[slot] = (uint32_t)(base + lo);
+    }
+}
+
+}  // namespace
+
+size_t cull_scratch_bytes(int64_t n) {
+    int64_t nchunks = (n + kChunk - 1) / kChunk;
+    return (size_t)(nchunks > 0 ? nchunks : 1) * sizeof(uint32_t);
+}
+
+cudaError_t launch_cull(int64_t n, const uint32_t* tiles_touched, const uint16_t* rect,
+                        const float* depth, const Frame& f, uint32_t* offsets, uint64_t* keys,
+                        uint32_t* vals, int64_t key_capacity, uint32_t* num_keys,
+                        uint32_t* status, void* scratch, cudaStream_t stream) {
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    uint32_t* sums = static_cast<uint32_t*>(scratch);
+    if (nchunks > 0) {
+        k_chunk_sums<<<(unsigned)nchunks, kScanThreads, 0, stream>>>(n, tiles_touched, sums);
+    }
+    k_chunk_scan<<<1, kTopThreads, 0, stream>>>(nchunks, n, sums, offsets, num_keys, key_capacity,
+                                               status);
+    if (nchunks > 0) {
+        k_emit<<<(unsigned)nchunks, kScanThreads, 0, stream>>>(
+            n, tiles_touched, reinterpret_cast<const uint2*>(rect), depth, sums, f.TX, offsets,
+            keys, vals, key_capacity);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ws

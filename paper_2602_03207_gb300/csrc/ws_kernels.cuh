@@ -1,0 +1,51 @@
+// Launchers of the render-path kernels (host side, called by ws_api.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ws_common.cuh"
+
+namespace ws {
+
+cudaError_t launch_preprocess(int64_t n, const float* means, const float* log_scales,
+                              const float* quats, const float* logits, const float* sh,
+                              const Frame& f, float* mean2d, float* conic, float* depth,
+                              float* rgb, float* opacity, uint16_t* rect,
+                              uint32_t* tiles_touched, cudaStream_t stream);
+
+// ---- compaction (scan of tiles_touched + key emission)
+size_t cull_scratch_bytes(int64_t n);
+cudaError_t launch_cull(int64_t n, const uint32_t* tiles_touched, const uint16_t* rect,
+                        const float* depth, const Frame& f, uint32_t* offsets, uint64_t* keys,
+                        uint32_t* vals, int64_t key_capacity, uint32_t* num_keys,
+                        uint32_t* status, void* scratch, cudaStream_t stream);
+
+// ---- radix sort
+size_t sort_scratch_bytes(int64_t key_capacity, int digit_bits);
+bool sort_digit_supported(int digit_bits);
+cudaError_t launch_sort(const uint32_t* num_keys, int64_t key_capacity, int begin_bit,
+                        int end_bit, int digit_bits, uint64_t* keys, uint32_t* vals,
+                        uint64_t* keys_alt, uint32_t* vals_alt, void* scratch, int* in_alt,
+                        cudaStream_t stream);
+
+// ---- rasterisation
+cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t key_capacity_hint,
+                             const uint64_t* keys, const uint32_t* vals, const float* mean2d,
+                             const float* conic, const float* opacity, const float* rgb,
+                             const Frame& f, uint32_t* ranges, float* image, float* t_final,
+                             uint32_t* n_contrib, cudaStream_t stream);
+
+// ---- backward
+size_t backward_scratch_bytes(int64_t key_capacity);
+cudaError_t launch_backward(int64_t n, const float* means, const float* log_scales, const float* quats,
+                            const float* sh, const Frame& f, const float* mean2d, const float* conic,
+                            const float* rgb, const float* opacity, const uint16_t* rect,
+                            const uint32_t* offsets, const uint32_t* tiles_touched,
+                            const uint32_t* vals, const uint32_t* ranges, const float* t_final,
+                            const uint32_t* n_contrib, const float* d_image, float* d_means,
+                            float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
+                            void* scratch, cudaStream_t stream);
+
+}  // namespace ws

@@ -1,0 +1,312 @@
+// Wait-free, deterministic LSD radix sort of (uint64 key, uint32 value)
+// pairs (paper §3.3.2).
+//
+// The paper's decomposition of the scatter position of element i with
+// digit d,
+//     pos = base_d + rank_i,   rank_i = prefix_wg + rank_local_i,
+// is kept exactly. Each pass is three dispatches:
+//   1. upsweep:   every block counts the digits of its tile of keys
+//                 (warp-private histograms in shared memory, warp-aggregated
+//                 with match.any so heavily repeated digits cost one update
+//                 per warp instruction) and writes one column of the
+//                 digit-major matrix hist[d][tile].
+//   2. scan:      one block per digit scans its row; the exclusive row
+//                 prefix is prefix_wg, the row total feeds base_d.
+//   3. downsweep: every block re-reads its tile, ranks each key among the
+//                 tile's equal digits in input order (rank_local), sorts the
+//                 tile by digit in shared memory and writes each digit run
+//                 to base_d + prefix_wg + position: consecutive threads write
+//                 consecutive addresses.
+// No block ever waits on another (no flags, no spinning) and no global
+// atomics are used, so the result is identical under any scheduling; the
+// order of equal keys is their input order.
+//
+// The key count lives in device memory (written by the compaction), so the
+// grids are sized by the capacity and blocks past the count return at once.
+#include "ws_common.cuh"
+#include "ws_kernels.cuh"
+
+namespace ws {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / kWarp;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per block
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_upsweep(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, int shift,
+               uint32_t mask, uint32_t* __restrict__ hist, int max_tiles) {
+    constexpr int R = 1 << BITS;
+    __shared__ uint32_t s_hist[kSortWarps][R];
+    const uint32_t n = *num_keys;
+    const int tile = blockIdx.x;
+    if ((int64_t)tile * kSortTile >= (int64_t)n) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_hist[0][0])[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)tile * kSortTile + warp * (kWarp * kSortItems);
+    uint32_t dig[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        int64_t idx = base + k * kWarp + lane;
+        dig[k] = idx < n ? (uint32_t)(__ldg(keys + idx) >> shift) & mask : (uint32_t)R;
+    }
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        uint32_t peers = __match_any_sync(kFull, dig[k]);
+        if (dig[k] < (uint32_t)R && lane == __ffs(peers) - 1) s_hist[warp][dig[k]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < R; d += kSortThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) s += s_hist[w][d];
+        hist[(size_t)d * max_tiles + tile] = s;
+    }
+}
+
+// One block per digit: exclusive scan of hist[d][0 .. tiles) in place, row
+// total into totals[d].
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_scan(const uint32_t* __restrict__ num_keys, uint32_t* __restrict__ hist,
+            uint32_t* __restrict__ totals, int max_tiles) {
+    __shared__ uint32_t s_red[kSortThreads / 32 + 1];
+    const uint32_t n = *num_keys;
+    const int tiles = (int)((n + kSortTile - 1) / kSortTile);
+    uint32_t* row = hist + (size_t)blockIdx.x * max_tiles;
+    uint32_t carry = 0;
+    constexpr int kPer = 4;
+    for (int start = 0; start < tiles; start += kSortThreads * kPer) {
+        uint32_t v[kPer];
+        uint32_t acc = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            int t = start + threadIdx.x * kPer + k;
+            v[k] = t < tiles ? row[t] : 0u;
+            acc += v[k];
+        }
+        uint32_t total;
+        uint32_t ex = block_exclusive_scan<kSortThreads>(acc, s_red, &total);
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            int t = start + threadIdx.x * kPer + k;
+            if (t < tiles) row[t] = carry + ex;
+            ex += v[k];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_downsweep(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                 uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                 const uint32_t* __restrict__ num_keys, int shift, uint32_t mask,
+                 const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals,
+                 int max_tiles) {
+    constexpr int R = 1 << BITS;
+    constexpr int kPerThread = R > kSortThreads ? R / kSortThreads : 1;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_raw);                  // [kSortTile]
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kSortTile);     // [kSortTile]
+    auto s_wh = reinterpret_cast<uint16_t (*)[R]>(s_vals + kSortTile);     // [warps][R] counts, then prefixes
+    uint32_t* s_start = reinterpret_cast<uint32_t*>(&s_wh[kSortWarps][0]); // [R] tile-local run starts
+    uint32_t* s_goff = s_start + R;  // [R] global position of each run minus its local start
+    uint32_t* s_red = s_goff + R;    // [warps + 1]
+
+    const uint32_t n = *num_keys;
+    const int tile = blockIdx.x;
+    const int64_t tile_base = (int64_t)tile * kSortTile;
+    if (tile_base >= (int64_t)n) return;
+    const int count = (int)(((int64_t)n - tile_base) < kSortTile ? ((int64_t)n - tile_base) : kSortTile);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_wh[0][0])[d] = 0;
+    __syncthreads();
+
+    // Load in warp-striped order: item k of lane l of warp w is element
+    // w*512 + k*32 + l of the tile, so (w, k, l) order is input order.
+    const int64_t base = tile_base + warp * (kWarp * kSortItems);
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems];
+    uint32_t dig[kSortItems];
+    uint16_t rnk[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        int64_t idx = base + k * kWarp + lane;
+        bool ok = idx < (int64_t)n;
+        key[k] = ok ? __ldg(keys_in + idx) : 0ull;
+        val[k] = ok ? __ldg(vals_in + idx) : 0u;
+        dig[k] = ok ? (uint32_t)(key[k] >> shift) & mask : (uint32_t)R;
+    }
+    // rank_local within the warp, in input order.
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        uint32_t d = dig[k];
+        uint32_t peers = __match_any_sync(kFull, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t prior = 0;
+        if (lane == leader && d < (uint32_t)R) prior = s_wh[warp][d];
+        prior = __shfl_sync(kFull, prior, leader);
+        rnk[k] = (uint16_t)(prior + __popc(peers & lt));
+        if (lane == leader && d < (uint32_t)R) s_wh[warp][d] = (uint16_t)(prior + __popc(peers));
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // Per digit: exclusive prefix over warps, tile count, block scan over
+    // digits -> tile-local run starts; global offsets base_d + prefix_wg.
+    uint32_t cnt[kPerThread];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        int d = threadIdx.x * kPerThread + j;
+        uint32_t run = 0;
+        if (d < R) {
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                uint32_t c = s_wh[w][d];
+                s_wh[w][d] = (uint16_t)run;
+                run += c;
+            }
+        }
+        cnt[j] = run;
+        acc += run;
+    }
+    uint32_t dummy;
+    uint32_t ex = block_exclusive_scan<kSortThreads>(acc, s_red, &dummy);
+    // base_d: exclusive scan of the digit totals of the whole pass.
+    uint32_t tacc = 0;
+    uint32_t tv[kPerThread];
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        int d = threadIdx.x * kPerThread + j;
+        tv[j] = d < R ? totals[d] : 0u;
+        tacc += tv[j];
+    }
+    uint32_t tex = block_exclusive_scan<kSortThreads>(tacc, s_red, &dummy);
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        int d = threadIdx.x * kPerThread + j;
+        if (d < R) {
+            s_start[d] = ex;
+            s_goff[d] = tex + hist[(size_t)d * max_tiles + tile] - ex;
+        }
+        ex += cnt[j];
+        tex += tv[j];
+    }
+    __syncthreads();
+
+    // Sort the tile by digit in shared memory.
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        uint32_t d = dig[k];
+        if (d < (uint32_t)R) {
+            uint32_t p = s_start[d] + s_wh[warp][d] + rnk[k];
+            s_keys[p] = key[k];
+            s_vals[p] = val[k];
+        }
+    }
+    __syncthreads();
+
+    // Write each digit run to pos = base_d + prefix_wg + local position.
+    for (int p = threadIdx.x; p < count; p += kSortThreads) {
+        uint64_t kk = s_keys[p];
+        uint32_t d = (uint32_t)(kk >> shift) & mask;
+        uint32_t pos = s_goff[d] + p;
+        keys_out[pos] = kk;
+        vals_out[pos] = s_vals[p];
+    }
+}
+
+template <int BITS>
+constexpr size_t downsweep_smem() {
+    return (size_t)kSortTile * 12 + (size_t)kSortWarps * (1 << BITS) * 2 + (size_t)(1 << BITS) * 8 +
+           (kSortThreads / 32 + 1) * 4;
+}
+
+struct SortScratch {
+    uint32_t* hist;
+    uint32_t* totals;
+};
+
+int max_tiles_for(int64_t capacity) { return (int)((capacity + kSortTile - 1) / kSortTile); }
+
+template <int BITS>
+cudaError_t sort_passes(const uint32_t* num_keys, int64_t capacity, int begin_bit, int end_bit,
+                        uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                        SortScratch s, int* in_alt, cudaStream_t stream) {
+    const int max_tiles = max_tiles_for(capacity);
+    constexpr size_t smem = downsweep_smem<BITS>();
+    static bool configured = false;  // one attribute call per instantiation
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_sort_downsweep<BITS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    uint64_t* kin = keys;
+    uint32_t* vin = vals;
+    uint64_t* kout = keys_alt;
+    uint32_t* vout = vals_alt;
+    int passes = 0;
+    for (int shift = begin_bit; shift < end_bit; shift += BITS) {
+        const int bits = end_bit - shift < BITS ? end_bit - shift : BITS;
+        const uint32_t mask = (1u << bits) - 1u;
+        if (max_tiles > 0) {
+            k_sort_upsweep<BITS><<<max_tiles, kSortThreads, 0, stream>>>(kin, num_keys, shift, mask,
+                                                                       s.hist, max_tiles);
+            k_sort_scan<<<1 << BITS, kSortThreads, 0, stream>>>(num_keys, s.hist, s.totals, max_tiles);
+            k_sort_downsweep<BITS><<<max_tiles, kSortThreads, smem, stream>>>(
+                kin, vin, kout, vout, num_keys, shift, mask, s.hist, s.totals, max_tiles);
+        }
+        uint64_t* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+        ++passes;
+    }
+    *in_alt = passes & 1;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool sort_digit_supported(int digit_bits) { return digit_bits >= 4 && digit_bits <= 8; }
+
+size_t sort_scratch_bytes(int64_t key_capacity, int digit_bits) {
+    const size_t R = (size_t)1 << digit_bits;
+    const size_t tiles = (size_t)max_tiles_for(key_capacity);
+    return (R * (tiles > 0 ? tiles : 1) + R) * sizeof(uint32_t);
+}
+
+cudaError_t launch_sort(const uint32_t* num_keys, int64_t key_capacity, int begin_bit,
+                        int end_bit, int digit_bits, uint64_t* keys, uint32_t* vals,
+                        uint64_t* keys_alt, uint32_t* vals_alt, void* scratch, int* in_alt,
+                        cudaStream_t stream) {
+    const size_t R = (size_t)1 << digit_bits;
+    const size_t tiles = (size_t)max_tiles_for(key_capacity);
+    SortScratch s;
+    s.hist = static_cast<uint32_t*>(scratch);
+    s.totals = s.hist + R * (tiles > 0 ? tiles : 1);
+    switch (digit_bits) {
+        case 4: return sort_passes<4>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 5: return sort_passes<5>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 6: return sort_passes<6>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 7: return sort_passes<7>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 8: return sort_passes<8>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ws

@@ -1,0 +1,194 @@
+"""Frame orchestration on top of the C ABI.
+
+``Renderer`` owns the device buffers of one resolution and issues the four
+C-ABI calls of a frame (ws_preprocess -> ws_cull -> ws_sort -> ws_rasterize)
+on the current CUDA stream. It holds no arithmetic of its own: torch only
+allocates memory and provides the stream.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import capi
+
+SCENE_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def scene_to_device(scene, device="cuda"):
+    """numpy scene dict -> contiguous float32 CUDA tensors."""
+    out = {}
+    for k in SCENE_KEYS:
+        out[k] = torch.as_tensor(scene[k], dtype=torch.float32).contiguous().to(device)
+    return out
+
+
+def tile_grid(width, height, tile):
+    return (width + tile - 1) // tile, (height + tile - 1) // tile
+
+
+def key_end_bit(width, height, tile):
+    """Keys are (tile id << 31) | depth bits; the sort covers bits [0, end)."""
+    tx, ty = tile_grid(width, height, tile)
+    tiles = tx * ty
+    return 31 + max(1, math.ceil(math.log2(tiles))) if tiles > 1 else 31
+
+
+class Renderer:
+    """Buffers and calls for frames of a fixed (n, width, height, tile)."""
+
+    def __init__(self, n, width, height, tile=16, digit_bits=8, key_capacity=None, dilation=0.3,
+                 guard=1.3, flags=0, device="cuda"):
+        self.n, self.width, self.height = int(n), int(width), int(height)
+        self.cfg = capi.config(tile=tile, digit_bits=digit_bits, dilation=dilation, guard=guard,
+                               flags=flags)
+        self.tile = tile
+        self.tx, self.ty = tile_grid(width, height, tile)
+        self.key_capacity = int(key_capacity if key_capacity is not None else max(1024, 4 * self.n))
+        self.end_bit = key_end_bit(width, height, tile)
+        d = torch.device(device)
+        n1 = max(self.n, 1)
+        cap = max(self.key_capacity, 1)
+        self.mean2d = torch.empty((n1, 4), dtype=torch.float32, device=d)
+        self.conic = torch.empty((n1, 3), dtype=torch.float32, device=d)
+        self.depth = torch.empty(n1, dtype=torch.float32, device=d)
+        self.rgb = torch.empty((n1, 3), dtype=torch.float32, device=d)
+        self.opacity = torch.empty(n1, dtype=torch.float32, device=d)
+        self.rect = torch.empty((n1, 4), dtype=torch.int16, device=d)       # uint16 payload
+        self.tiles_touched = torch.empty(n1, dtype=torch.int32, device=d)   # uint32 payload
+        self.offsets = torch.empty(self.n + 1, dtype=torch.int32, device=d)
+        self.keys = torch.empty(cap, dtype=torch.int64, device=d)           # uint64 payload
+        self.vals = torch.empty(cap, dtype=torch.int32, device=d)
+        self.keys_alt = torch.empty(cap, dtype=torch.int64, device=d)
+        self.vals_alt = torch.empty(cap, dtype=torch.int32, device=d)
+        self.num_keys = torch.zeros(4, dtype=torch.int32, device=d)
+        self.ranges = torch.empty((self.tx * self.ty, 2), dtype=torch.int32, device=d)
+        self.image = torch.empty((height, width, 3), dtype=torch.float32, device=d)
+        self.t_final = torch.empty((height, width), dtype=torch.float32, device=d)
+        self.n_contrib = torch.empty((height, width), dtype=torch.int32, device=d)
+        self._cam_probe = None
+        self.workspace = None
+        self.sorted_in_alt = False
+
+    def _ensure_workspace(self, cam):
+        if self.workspace is None:
+            nbytes = capi.ws_workspace_bytes(self.n, self.key_capacity, cam, self.cfg)
+            if nbytes == 0:
+                raise ValueError("ws_workspace_bytes rejected the configuration")
+            self.workspace = torch.zeros(nbytes, dtype=torch.uint8, device=self.image.device)
+
+    # ------------------------------------------------------------ stages
+    def preprocess(self, scene, cam, stream=None):
+        capi.ws_preprocess(self.n, scene["means"], scene["log_scales"], scene["quats"],
+                           scene["opacity_logits"], scene["sh"], cam, self.cfg, self.mean2d, self.conic,
+                           self.depth, self.rgb, self.opacity, self.rect, self.tiles_touched, stream)
+
+    def cull(self, cam, stream=None):
+        self._ensure_workspace(cam)
+        capi.ws_cull(self.n, self.tiles_touched, self.rect, self.depth, cam, self.cfg, self.offsets,
+                     self.keys, self.vals, self.key_capacity, self.num_keys, self.workspace, stream)
+
+    def sort(self, stream=None):
+        self.sorted_in_alt = capi.ws_sort(self.num_keys, self.key_capacity, 0, self.end_bit, self.keys,
+                                          self.vals, self.keys_alt, self.vals_alt, self.cfg,
+                                          self.workspace, stream)
+
+    @property
+    def sorted_keys(self):
+        return self.keys_alt if self.sorted_in_alt else self.keys
+
+    @property
+    def sorted_vals(self):
+        return self.vals_alt if self.sorted_in_alt else self.vals
+
+    def rasterize(self, cam, stream=None):
+        capi.ws_rasterize(self.num_keys, self.sorted_keys, self.sorted_vals, self.mean2d, self.conic,
+                          self.opacity, self.rgb, cam, self.cfg, self.ranges, self.image, self.t_final,
+                          self.n_contrib, stream)
+
+    def forward(self, scene, cam_dict, stream=None):
+        """One frame; returns the image tensor (H, W, 3). Asynchronous."""
+        cam = capi.camera(cam_dict)
+        if cam.width != self.width or cam.height != self.height:
+            raise ValueError("camera resolution differs from the renderer's")
+        self.preprocess(scene, cam, stream)
+        self.cull(cam, stream)
+        self.sort(stream)
+        self.rasterize(cam, stream)
+        return self.image
+
+    def backward(self, scene, cam_dict, d_image, stream=None):
+        """Gradients of a loss w.r.t. the Gaussians for the frame last
+        rendered by forward() with the same scene and camera; d_image is
+        dL/dimage (H, W, 3). Returns a dict of gradient tensors."""
+        cam = capi.camera(cam_dict)
+        d = self.image.device
+        n1 = max(self.n, 1)
+        g = {"means": torch.empty((n1, 3), dtype=torch.float32, device=d),
+             "log_scales": torch.empty((n1, 3), dtype=torch.float32, device=d),
+             "quats": torch.empty((n1, 4), dtype=torch.float32, device=d),
+             "opacity_logits": torch.empty(n1, dtype=torch.float32, device=d),
+             "sh": torch.empty((n1, 16, 3), dtype=torch.float32, device=d)}
+        d_image = d_image.contiguous()
+        capi.ws_rasterize_backward(self.n, scene["means"], scene["log_scales"], scene["quats"],
+                                   scene["opacity_logits"], scene["sh"], cam, self.cfg, self.mean2d, self.conic,
+                                   self.rgb, self.opacity, self.rect, self.offsets, self.tiles_touched,
+                                   self.sorted_vals, self.ranges, self.t_final, self.n_contrib, d_image,
+                                   self.key_capacity, g["means"], g["log_scales"], g["quats"],
+                                   g["opacity_logits"], g["sh"], self.workspace, stream)
+        return {k: v[:self.n] for k, v in g.items()}
+
+    def check_status(self, stream=None):
+        """Synchronises and raises if the frame overflowed its key capacity."""
+        flags = capi.ws_read_status(self.workspace, clear=False, stream=stream)
+        if flags & capi.WS_FLAG_CAPACITY:
+            raise capi.WsError("frame", capi.WS_ERR_CAPACITY)
+        return flags
+
+    def key_count(self):
+        return int(self.num_keys[0].item())
+
+    def total_pairs(self):
+        return int(self.offsets[self.n].item()) & 0xFFFFFFFF
+
+
+def render(scene, cam_dict, tile=16, digit_bits=8, key_capacity=None, flags=0):
+    """Render one frame of a device scene dict; returns (image, renderer).
+
+    Raises when the pair list overflows the key capacity (after a sync)."""
+    n = scene["means"].shape[0]
+    r = Renderer(n, cam_dict["width"], cam_dict["height"], tile=tile, digit_bits=digit_bits,
+                 key_capacity=key_capacity, flags=flags, device=scene["means"].device)
+    img = r.forward(scene, cam_dict)
+    r.check_status()
+    return img, r
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable frame: image = render(means, log_scales, quats,
+    opacity_logits, sh). The renderer's buffers hold the frame's
+    intermediates between forward and backward, so one renderer serves one
+    frame in flight at a time."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, renderer, cam_dict):
+        scene = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
+                 "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
+                 "sh": sh.contiguous()}
+        img = renderer.forward(scene, cam_dict)
+        renderer.check_status()
+        ctx.renderer, ctx.cam, ctx.scene = renderer, cam_dict, scene
+        return img.clone()
+
+    @staticmethod
+    def backward(ctx, d_image):
+        g = ctx.renderer.backward(ctx.scene, ctx.cam, d_image)
+        return g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], None, None
+
+
+def render_differentiable(params, renderer, cam_dict):
+    """params: dict of leaf tensors (means, log_scales, quats,
+    opacity_logits, sh); returns the image with autograd attached."""
+    return RenderFunction.apply(params["means"], params["log_scales"], params["quats"],
+                                params["opacity_logits"], params["sh"], renderer, cam_dict)

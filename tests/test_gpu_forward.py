@@ -1,0 +1,196 @@
+"""GPU parity of the forward render path (C ABI) against the FP64 oracle.
+
+Tolerances: cull mask, tile rectangles, depth keys, emitted pairs and the
+sort permutation are bit-exact on every decision the oracle does not flag
+as within float32 rounding of its threshold (flagged ones may go either
+way); the image is within 2e-4 per channel (max abs) of the oracle, or of
+its alternative for a pixel with one flagged 1/255 decision.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_03207_gb300 import synthetic as S
+
+from helpers import IMAGE_ATOL, compare_image, fetch, gpu_frame, last_gid
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_preprocess(g, ref, n_amb_max=None):
+    p = ref["proj"]
+    amb = p["amb"].astype(bool)
+    vis_ref = p["touched"] > 0
+    vis_gpu = g["touched"] > 0
+    # depth: identical float32 for every Gaussian
+    np.testing.assert_array_equal(g["depth"].view(np.uint32), p["depth"].view(np.uint32))
+    # cull mask bit-exact on unambiguous decisions
+    assert np.array_equal(vis_gpu[~amb], vis_ref[~amb])
+    both = vis_ref & vis_gpu & ~amb
+    np.testing.assert_array_equal(g["rect"][both], p["rect"][both])
+    np.testing.assert_array_equal(g["touched"][both], p["touched"][both])
+    # ambiguous ones: each bound within one tile of the oracle's
+    a = amb & vis_ref & vis_gpu
+    if a.any():
+        assert np.abs(g["rect"][a] - p["rect"][a]).max() <= 1
+    vv = vis_ref & vis_gpu
+    np.testing.assert_allclose(g["mean2d"][vv], p["mean2d"][vv], rtol=0, atol=2e-6)
+    # conic: what the blend uses is the quadratic form q = d^T Q d; its
+    # relative error over all directions d is the spectral radius of
+    # Sigma'_ref (Q_gpu - Q_ref), bounded here by 1e-4.
+    cov = p["cov2d"][vv]
+    dq = g["conic"][vv].astype(np.float64) - p["conic"][vv]
+    S2 = np.stack([np.stack([cov[:, 0], cov[:, 1]], -1), np.stack([cov[:, 1], cov[:, 2]], -1)], -2)
+    D2 = np.stack([np.stack([dq[:, 0], dq[:, 1]], -1), np.stack([dq[:, 1], dq[:, 2]], -1)], -2)
+    metric = np.abs(np.linalg.eigvals(S2 @ D2)).max(-1)
+    assert metric.max() <= 1e-4, metric.max()
+    np.testing.assert_allclose(g["rgb"][vv], p["rgb"][vv], rtol=0, atol=2e-6)
+    np.testing.assert_allclose(g["opacity"][vv], p["opacity"][vv], rtol=2e-6, atol=0)
+    if n_amb_max is not None:
+        assert amb.sum() <= n_amb_max
+
+
+def _check_emission(g, ref):
+    p = ref["proj"]
+    touched_g = g["touched"]
+    np.testing.assert_array_equal(np.diff(g["offsets"]), touched_g)
+    same = (p["amb"] == 0) & (touched_g == p["touched"])
+    kg = np.repeat(same, touched_g)
+    kr = np.repeat(same, p["touched"])
+    np.testing.assert_array_equal(g["keys"][kg], ref["keys"][kr])
+    np.testing.assert_array_equal(g["vals"][kg], ref["vals"][kr])
+
+
+def _check_sort(g):
+    k, v = oracle.sort_pairs(g["keys"], g["vals"])
+    np.testing.assert_array_equal(g["sorted_keys"], k)
+    np.testing.assert_array_equal(g["sorted_vals"], v)
+
+
+def test_small_forward_parity():
+    """10,000 Gaussians, 256x256, 16x16 tiles: every stage against the oracle."""
+    scene, cam = S.small_forward()
+    r = gpu_frame(scene, cam)
+    g = fetch(r)
+    ref = oracle.render(scene, cam)
+    _check_preprocess(g, ref, n_amb_max=20)
+    _check_emission(g, ref)
+    _check_sort(g)
+    st = compare_image(g, ref)
+    assert st["n_bad"] == 0, st
+    assert st["max_err_clean"] <= IMAGE_ATOL
+    assert st["n_multi"] <= 0.001 * st["n_pix"]
+    ok = ref["n_amb"] == 0
+    np.testing.assert_array_equal(last_gid(g, 256, 256, 16)[ok], ref["last_gid"][ok])
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_tile_sizes(tile):
+    scene, cam = S.small_forward()
+    sub = {k: v[:3000] for k, v in scene.items()}
+    g = fetch(gpu_frame(sub, cam, tile=tile, key_capacity=16 * len(sub["means"])))
+    ref = oracle.render(sub, cam, tile=tile)
+    _check_preprocess(g, ref)
+    _check_emission(g, ref)
+    _check_sort(g)
+    st = compare_image(g, ref)
+    assert st["n_bad"] == 0, st
+
+
+def test_digit_widths_give_identical_frames():
+    """The sort's digit width changes the pass structure, never the result."""
+    scene, cam = S.small_forward()
+    imgs = []
+    for bits in (4, 5, 6, 7, 8):
+        g = fetch(gpu_frame(scene, cam, digit_bits=bits))
+        imgs.append((g["image"], g["sorted_keys"], g["sorted_vals"]))
+    for im, k, v in imgs[1:]:
+        np.testing.assert_array_equal(im, imgs[0][0])
+        np.testing.assert_array_equal(k, imgs[0][1])
+        np.testing.assert_array_equal(v, imgs[0][2])
+
+
+def test_ragged_resolution_and_background():
+    """A 100x75 image (partial tiles on two edges), a coloured background and
+    a camera looking at the scene off-centre."""
+    scene = S.uniform_scene(4000, seed=31)
+    cam = S.look_at_camera((2.0, -2.5, 1.0), (0.2, 0.1, 0.0), 100, 75, bg=(0.2, 0.5, 0.9))
+    g = fetch(gpu_frame(scene, cam))
+    ref = oracle.render(scene, cam)
+    _check_preprocess(g, ref)
+    _check_sort(g)
+    st = compare_image(g, ref)
+    assert st["n_bad"] == 0, st
+
+
+def test_empty_and_fully_culled_scenes():
+    """n = 0 and a scene whose every splat is below 1/255 give the background."""
+    cam = dict(S.small_forward()[1])
+    cam["bg"] = (0.25, 0.5, 0.75)
+    scene = S.uniform_scene(0, seed=1)
+    g = fetch(gpu_frame(scene, cam))
+    assert g["num_keys"] == 0
+    np.testing.assert_array_equal(g["image"], np.broadcast_to(np.float32(cam["bg"]), g["image"].shape))
+    scene = S.uniform_scene(500, seed=2)
+    scene["opacity_logits"][:] = -7.0
+    g = fetch(gpu_frame(scene, cam))
+    assert g["num_keys"] == 0 and (g["touched"] == 0).all()
+    np.testing.assert_array_equal(g["t_final"], 1.0)
+
+
+def test_single_splat_and_offscreen():
+    """One splat centred on a pixel centre (C = c * min(.99, sigma)) and one
+    fully outside the viewport (culled)."""
+    scene = S.uniform_scene(2, seed=3)
+    scene["means"][:] = [[(10.5 - 128) / 256 * 3.0, (20.5 - 128) / 256 * 3.0, 0.0], [50.0, 0.0, 0.0]]
+    scene["log_scales"][:] = -4.0
+    scene["opacity_logits"][:] = 0.7
+    _, cam = S.small_forward()
+    g = fetch(gpu_frame(scene, cam))
+    ref = oracle.render(scene, cam)
+    assert list(g["touched"] > 0) == [True, False]
+    assert abs(g["image"][20, 10] - ref["image"][20, 10]).max() <= 1e-5
+    st = compare_image(g, ref)
+    assert st["n_bad"] == 0, st
+
+
+def test_capacity_overflow_is_reported():
+    from paper_2602_03207_gb300 import capi
+    scene, cam = S.small_forward()
+    with pytest.raises(capi.WsError):
+        gpu_frame(scene, cam, key_capacity=1000)
+
+
+def test_frames_are_bitwise_deterministic():
+    scene, cam = S.small_forward()
+    a = fetch(gpu_frame(scene, cam))
+    b = fetch(gpu_frame(scene, cam))
+    for k in ("image", "t_final", "n_contrib", "sorted_keys", "sorted_vals", "keys", "vals"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_hd_workload_sampled():
+    """The 1,000,000-Gaussian 1920x1080 workload in the benchmark's launch
+    configuration (16x16 tiles, 8-bit digits): every Gaussian's
+    pre-processing, the whole pair list and sort, and the image on 96
+    sampled tiles (the densest 32 plus 64 seeded ones) against the oracle."""
+    scene = S.hd_scene()
+    cam = S.hd_camera(0)
+    r = gpu_frame(scene, cam)
+    g = fetch(r)
+    tx, ty = (1920 + 15) // 16, (1080 + 15) // 16
+    counts = g["ranges"][:, 1] - g["ranges"][:, 0]
+    dense = np.argsort(-counts, kind="stable")[:32]
+    rng = np.random.default_rng(77)
+    tiles = np.unique(np.concatenate([dense, rng.choice(tx * ty, 64, replace=False)]))
+    ref = oracle.render(scene, cam, tile_list=tiles)
+    _check_preprocess(g, ref, n_amb_max=int(0.005 * len(scene["means"])))
+    _check_emission(g, ref)
+    _check_sort(g)
+    mask = np.zeros((1080, 1920), bool)
+    for t in tiles:
+        y0, x0 = (t // tx) * 16, (t % tx) * 16
+        mask[y0:y0 + 16, x0:x0 + 16] = True
+    st = compare_image(g, ref, tile_mask=mask)
+    assert st["n_bad"] == 0, st
+    assert st["n_multi"] <= 0.001 * st["n_pix"]
