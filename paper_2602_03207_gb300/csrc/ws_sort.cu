@@ -23,6 +23,8 @@
 //
 // The key count lives in device memory (written by the compaction), so the
 // grids are sized by the capacity and blocks past the count return at once.
+#include <atomic>
+
 #include "ws_common.cuh"
 #include "ws_kernels.cuh"
 
@@ -250,12 +252,17 @@ cudaError_t sort_passes(const uint32_t* num_keys, int64_t capacity, int begin_bi
                         SortScratch s, int* in_alt, cudaStream_t stream) {
     const int max_tiles = max_tiles_for(capacity);
     constexpr size_t smem = downsweep_smem<BITS>();
-    static bool configured = false;  // one attribute call per instantiation
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_sort_downsweep<BITS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The dynamic shared-memory limit is a per-device function attribute:
+    // set it once per (instantiation, device).
+    static std::atomic<uint64_t> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (!(configured.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(k_sort_downsweep<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured.fetch_or(bit, std::memory_order_acq_rel);
     }
     uint64_t* kin = keys;
     uint32_t* vin = vals;
