@@ -164,6 +164,27 @@ ws_status ws_sort(const uint32_t *num_keys, int64_t key_capacity, int32_t begin_
                   uint32_t *vals_alt, const ws_config *cfg, void *workspace,
                   int32_t *result_in_alt, void *stream);
 
+/* ws_sort without a workspace, for callers that cannot allocate device
+ * memory: code running inside an engine that owns every device allocation
+ * and hands over only its input and output buffers, or a real-time frame
+ * loop that must not call cudaMalloc (which can synchronise the device).
+ * The paper has no counterpart; it is the same sort as ws_sort, with the
+ * histogram scratch held in a static device array inside the library
+ * (2 MiB + 1 KiB, kept by every GPU that loads the library until the process
+ * exits). The caller still passes the keys, values and ping-pong buffers.
+ * key_capacity must not exceed ws_sort_noalloc_max_keys() (8,388,608);
+ * larger values return WS_ERR_INVALID_ARG. digit_bits: 4..8. Allocates
+ * nothing. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture. All calls on one device share the array: calls that overlap on
+ * the GPU (different streams, concurrent graphs) race and must be ordered
+ * by the caller. */
+int64_t ws_sort_noalloc_max_keys(void);
+ws_status ws_sort_noalloc(const uint32_t *num_keys, int64_t key_capacity, int32_t begin_bit,
+                          int32_t end_bit, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                          uint32_t *vals_alt, int32_t digit_bits, int32_t *result_in_alt,
+                          void *stream);
+
 /* Rasterisation stage (§3.4 with §2.1's compositing), per 16x16 (tile^2)
  * pixel tile, front to back over the tile's depth-sorted list:
  *   a = min(0.99, sigma exp(-q/2)), q = d^T conic d, d = pixel centre -

@@ -25,7 +25,8 @@ WS_FLAG_CAPACITY, WS_FLAG_TIMEOUT = 1, 2
 WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL = 1, 2
 
 EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_preprocess", "ws_cull",
-           "ws_sort", "ws_rasterize", "ws_rasterize_backward", "ws_read_status")
+           "ws_sort", "ws_sort_noalloc", "ws_sort_noalloc_max_keys", "ws_rasterize",
+           "ws_rasterize_backward", "ws_read_status")
 
 
 class WsError(RuntimeError):
@@ -86,6 +87,9 @@ def lib():
             L.ws_rasterize.argtypes = [P, P, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
             L.ws_rasterize_backward.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P, P, P,
                                                 P, P, P, I64, P, P, P, P, P, P, P]
+            L.ws_sort_noalloc.argtypes = [P, I64, I32, I32, P, P, P, P, I32, C.POINTER(I32), P]
+            L.ws_sort_noalloc.restype = I32
+            L.ws_sort_noalloc_max_keys.restype = I64
             L.ws_read_status.argtypes = [P, C.POINTER(U32), I32, P]
             for name in ("ws_preprocess", "ws_cull", "ws_sort", "ws_rasterize", "ws_rasterize_backward",
                          "ws_read_status"):
@@ -142,6 +146,20 @@ def ws_sort(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, va
         _ptr(num_keys), int(key_capacity), int(begin_bit), int(end_bit), _ptr(keys), _ptr(vals),
         _ptr(keys_alt), _ptr(vals_alt), C.byref(cfg), _ptr(workspace), C.byref(in_alt),
         _stream(stream)))
+    return bool(in_alt.value)
+
+
+def ws_sort_noalloc_max_keys() -> int:
+    return int(lib().ws_sort_noalloc_max_keys())
+
+
+def ws_sort_noalloc(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, digit_bits=8,
+                    stream=None) -> bool:
+    """Workspace-free ws_sort (library-held scratch); True when the result is in the _alt buffers."""
+    in_alt = C.c_int32(0)
+    _check("ws_sort_noalloc", lib().ws_sort_noalloc(
+        _ptr(num_keys), int(key_capacity), int(begin_bit), int(end_bit), _ptr(keys), _ptr(vals),
+        _ptr(keys_alt), _ptr(vals_alt), int(digit_bits), C.byref(in_alt), _stream(stream)))
     return bool(in_alt.value)
 
 

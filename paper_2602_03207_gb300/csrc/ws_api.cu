@@ -172,6 +172,28 @@ ws_status ws_sort(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_
     return cuda_status(e);
 }
 
+int64_t ws_sort_noalloc_max_keys(void) { return ws::sort_noalloc_max_keys(); }
+
+ws_status ws_sort_noalloc(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_bit, int32_t end_bit,
+                          uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                          int32_t digit_bits, int32_t* result_in_alt, void* stream) {
+    if (!ws::sort_digit_supported(digit_bits)) return WS_ERR_UNSUPPORTED;
+    if (key_capacity < 0 || key_capacity > ws::sort_noalloc_max_keys() || begin_bit < 0 || end_bit > 64 ||
+        begin_bit >= end_bit || !result_in_alt)
+        return WS_ERR_INVALID_ARG;
+    if (!num_keys || !aligned16(num_keys)) return WS_ERR_INVALID_ARG;
+    if (key_capacity > 0) {
+        const void* kp[] = {keys, vals, keys_alt, vals_alt};
+        for (const void* p : kp)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    int in_alt = 0;
+    cudaError_t e = ws::launch_sort_noalloc(num_keys, key_capacity, begin_bit, end_bit, digit_bits, keys, vals,
+                                            keys_alt, vals_alt, &in_alt, static_cast<cudaStream_t>(stream));
+    *result_in_alt = in_alt;
+    return cuda_status(e);
+}
+
 ws_status ws_rasterize(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals,
                        const float* mean2d, const float* conic, const float* opacity, const float* rgb,
                        const ws_camera* cam, const ws_config* cfg, uint32_t* ranges, float* image,

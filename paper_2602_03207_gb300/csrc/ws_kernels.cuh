@@ -30,6 +30,14 @@ cudaError_t launch_sort(const uint32_t* num_keys, int64_t key_capacity, int begi
                         uint64_t* keys_alt, uint32_t* vals_alt, void* scratch, int* in_alt,
                         cudaStream_t stream);
 
+// allocation-free variant: histogram scratch in a static device array
+int64_t sort_noalloc_max_keys();
+size_t sort_noalloc_scratch_bytes();
+cudaError_t launch_sort_noalloc(const uint32_t* num_keys, int64_t key_capacity, int begin_bit,
+                                int end_bit, int digit_bits, uint64_t* keys, uint32_t* vals,
+                                uint64_t* keys_alt, uint32_t* vals_alt, int* in_alt,
+                                cudaStream_t stream);
+
 // ---- rasterisation
 cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t key_capacity_hint,
                              const uint64_t* keys, const uint32_t* vals, const float* mean2d,

@@ -24,6 +24,7 @@
 // The key count lives in device memory (written by the compaction), so the
 // grids are sized by the capacity and blocks past the count return at once.
 #include <atomic>
+#include <mutex>
 
 #include "ws_common.cuh"
 #include "ws_kernels.cuh"
@@ -306,6 +307,78 @@ cudaError_t launch_sort(const uint32_t* num_keys, int64_t key_capacity, int begi
     SortScratch s;
     s.hist = static_cast<uint32_t*>(scratch);
     s.totals = s.hist + R * (tiles > 0 ? tiles : 1);
+    switch (digit_bits) {
+        case 4: return sort_passes<4>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 5: return sort_passes<5>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 6: return sort_passes<6>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 7: return sort_passes<7>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 8: return sort_passes<8>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of launch_sort (the ws_sort_noalloc entry point).
+//
+// Some callers cannot allocate device memory for scratch: code that runs
+// inside a host engine which owns every device allocation (a plugin handed
+// only its input and output buffers), or a real-time frame loop that must
+// not call cudaMalloc, which can synchronise the device and stall the frame.
+// For them the sort's histogram scratch lives in the file-scope array below,
+// sized for at most kNoAllocMaxKeys keys. Every GPU that loads this library
+// holds the array until the process exits, and all calls on a device share
+// it, so two such sorts that overlap on the GPU race on it. Nothing in it
+// needs clearing between calls: each pass writes every histogram entry it
+// later reads (the tiles below the key count) before reading it.
+namespace {
+
+constexpr int64_t kNoAllocMaxKeys = int64_t(1) << 23;  // 8,388,608 keys
+constexpr int kNoAllocMaxTiles = (int)((kNoAllocMaxKeys + kSortTile - 1) / kSortTile);
+constexpr int kNoAllocMaxDigits = 256;  // 8-bit digits at most
+constexpr size_t kNoAllocWords = (size_t)kNoAllocMaxDigits * kNoAllocMaxTiles + kNoAllocMaxDigits;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+// 2 MiB + 1 KiB per device: the digit-major histogram matrix for
+// kNoAllocMaxKeys keys plus the digit totals.
+static __device__ __align__(256) uint32_t ws_sort_noalloc_scratch[kNoAllocWords];
+
+int64_t sort_noalloc_max_keys() { return kNoAllocMaxKeys; }
+
+size_t sort_noalloc_scratch_bytes() { return sizeof(uint32_t) * kNoAllocWords; }
+
+cudaError_t launch_sort_noalloc(const uint32_t* num_keys, int64_t key_capacity, int begin_bit,
+                                int end_bit, int digit_bits, uint64_t* keys, uint32_t* vals,
+                                uint64_t* keys_alt, uint32_t* vals_alt, int* in_alt,
+                                cudaStream_t stream) {
+    if (key_capacity > kNoAllocMaxKeys || digit_bits > 8) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    uint32_t* base = nullptr;
+    {
+        // Set-up, once per device with that device current: the host-side
+        // name of the array is not a device address, so look the address up.
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, ws_sort_noalloc_scratch);
+            if (e != cudaSuccess) return e;
+            g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    const size_t R = (size_t)1 << digit_bits;
+    const size_t tiles = (size_t)max_tiles_for(key_capacity);
+    SortScratch s;
+    s.hist = base;
+    s.totals = base + R * (tiles > 0 ? tiles : 1);
     switch (digit_bits) {
         case 4: return sort_passes<4>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
         case 5: return sort_passes<5>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
