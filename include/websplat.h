@@ -128,7 +128,7 @@ ws_status ws_preprocess(int64_t n, const float *means, const float *log_scales,
                         uint16_t *rect, uint32_t *tiles_touched, void *stream);
 
 /* Compaction of the surviving splats into the <tile, splat> pair list
- * (§3.2: "the alive primitives are written into a buffer"; §3.4 describes
+ * (§3.2 compacts the survivors of culling into a buffer; §3.4 describes
  * the tile-based pair list this path uses). A wait-free two-level scan
  * (one dispatch per level, no inter-block waiting, no global atomics) of
  * tiles_touched gives

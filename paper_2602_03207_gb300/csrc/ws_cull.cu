@@ -1,6 +1,6 @@
 // Compaction of the surviving splats into the <tile, splat> pair list.
 //
-// §3.2 writes the "alive primitives" into a buffer; this path writes one
+// §3.2 compacts the splats that survive culling into a buffer; this path writes one
 // (tile, depth) key per overlapped tile (the tile decomposition §3.4
 // describes). The slot of every pair comes from an exclusive scan of
 // tiles_touched, computed wait-free in the spirit of §3.3.2's hierarchical
