@@ -152,12 +152,71 @@ def blend_work(fetched, width, height, tile):
     return float(np.sum(np.maximum(wx, 0) * np.maximum(wy, 0)))
 
 
+# ------------------------------------------------------- multi-rank helpers
+
+def rank_pose(rank, step, n_poses=8):
+    """Pose rendered by `rank` at `step`: ranks start at different poses and
+    each renders its own frames (no frame is shared, no collective)."""
+    return (rank * 3 + step) % n_poses
+
+
+def max_over_ranks(seconds, dist=None, device=None):
+    """Slowest rank's time (the job's time); identity for one process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(seconds)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second of the slowest rank."""
+    return units_per_rank * world / seconds
+
+
 # ------------------------------------------------------------------ ours
+
+def sort_only(dev, steps=50, digit_bits=9):
+    """Sort-only throughput: the 4,194,304-key (tile, depth) array, 44 bits,
+    timed with CUDA events around each ws_sort call (input copied in
+    between, outside the timed span)."""
+    import torch
+    from paper_2602_03207_gb300 import capi, synthetic as S
+    k4, v4 = S.sort_keys()
+    n = k4.size
+    kk = torch.from_numpy(k4.view(np.int64)).to(dev)
+    vv = torch.from_numpy(v4.view(np.int32)).to(dev)
+    k1, v1, k2, v2 = torch.empty_like(kk), torch.empty_like(vv), torch.empty_like(kk), torch.empty_like(vv)
+    num = torch.tensor([n, 0, 0, 0], dtype=torch.int32, device=dev)
+    cfg = capi.config(digit_bits=digit_bits)
+    cam = capi.camera(S.small_forward()[1])
+    ws = torch.zeros(capi.ws_workspace_bytes(0, n, cam, cfg), dtype=torch.uint8, device=dev)
+    ts = []
+    for it in range(steps + 5):
+        k1.copy_(kk)
+        v1.copy_(vv)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        capi.ws_sort(num, n, 0, 44, k1, v1, k2, v2, cfg, ws)
+        b.record()
+        torch.cuda.synchronize()
+        if it >= 5:
+            ts.append(a.elapsed_time(b))
+    ts.sort()
+    med = ts[len(ts) // 2] * 1e-3
+    passes = math.ceil(44 / digit_bits)
+    gbs = sort_bytes(n, passes) / med / 1e9
+    return {"keys": n, "key_bits": 44, "digit_bits": digit_bits, "median_ms": round(med * 1e3, 4),
+            "gkeys_s": round(n / med / 1e9, 3), "achieved_gbs": round(gbs, 1)}
+
 
 def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2602_03207_gb300 import capi, render
+    if args.workload == "batch":
+        return run_batch(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -186,11 +245,11 @@ def run_ours(args):
     r = render.Renderer(n, W, H, tile=args.tile, digit_bits=args.digit_bits, key_capacity=cap, device=dev)
     stream = torch.cuda.current_stream(dev)
     passes = math.ceil(r.end_bit / args.digit_bits)
-    launches_per_frame = 1 + 3 + 3 * passes + 2
+    launches_per_frame = 1 + 3 + 3 * passes + 3  # preprocess, cull (3), sort (3 per pass), raster (3)
 
     # warm-up
     for i in range(args.warmup):
-        r.forward(scene, cams[(rank + i) % 8])
+        r.forward(scene, cams[rank_pose(rank, i)])
     r.check_status()
 
     # stage timing events (per step, on the launching stream)
@@ -203,7 +262,7 @@ def run_ours(args):
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
         for i in range(args.steps):
-            cam = capi.camera(cams[(rank * 3 + i) % 8])
+            cam = capi.camera(cams[rank_pose(rank, i)])
             e = ev[i]
             e[0].record(stream)
             r.preprocess(scene, cam)
@@ -225,12 +284,9 @@ def run_ours(args):
         for j, s in enumerate(STAGES):
             stage_ms[s] += e[j].elapsed_time(e[j + 1])
     stage_ms = {s: v / args.steps for s, v in stage_ms.items()}
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist if world > 1 else None, dev)
     frames = args.steps * world
-    value = frames / elapsed
+    value = whole_job_rate(args.steps, world, elapsed)
 
     # end to end through the public API: pinned host scene in, image out
     e2e = None
@@ -255,16 +311,12 @@ def run_ours(args):
         for i in range(k2):
             for k in render.SCENE_KEYS:
                 dscene[k].copy_(host[k], non_blocking=True)
-            r.forward(dscene, cams[(rank + i) % 8])
+            r.forward(dscene, cams[rank_pose(rank, i)])
             himg.copy_(r.image, non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize()
-        t2 = a.elapsed_time(b) / 1e3
-        if world > 1:
-            t = torch.tensor([t2], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t2 = float(t.item())
-        e2e = {"value": k2 * world / t2, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        t2 = max_over_ranks(a.elapsed_time(b) / 1e3, dist if world > 1 else None, dev)
+        e2e = {"value": whole_job_rate(k2, world, t2), "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     result = None
     if rank == 0:
@@ -350,6 +402,7 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    out["sort_only"] = sort_only(r.image.device, digit_bits=args.digit_bits)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
     return out
@@ -367,6 +420,93 @@ def cpu_baseline(args, frames=2):
     dt = time.perf_counter() - t
     return {"value": round(frames / dt, 4), "unit": "frames/s", "cores": 1, "kind": "oracle",
             "sample": f"{frames} full frames (poses 0..{frames - 1}) of the same workload, FP64 C oracle"}
+
+
+# ------------------------------------------------------------ batched views
+
+def run_batch(args):
+    """Batched forward + backward of the 2,000,000-Gaussian scene over 64
+    seeded views (uneven resolutions 320x240 .. 1920x1080): one training step
+    (forward, L2 residual, backward, gradients summed over views) replayed as
+    a CUDA graph with the autotuned tile size / digit width, against the plain
+    path of 64 per-view forward + backward calls (per-view gradients, not
+    summed: the comparison favours the plain path)."""
+    import torch
+    from paper_2602_03207_gb300 import autotune, batch, capi, render, synthetic as S
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    scene_np = S.batch_scene()
+    cams = S.batch_views()
+    n = scene_np["means"].shape[0]
+    scene = render.scene_to_device(scene_np, dev)
+    rng = np.random.default_rng(9)
+    targets = [torch.as_tensor(rng.random((c["height"], c["width"], 3), dtype=np.float32), device=dev)
+               for c in cams]
+    tgt = torch.cat([t.reshape(-1) for t in targets])
+    log = (lambda m: print(m, file=sys.stderr, flush=True))
+    best = autotune.tune(scene, cams, tgt, log=log)
+    b = batch.BatchRenderer(n, cams, tile=best["tile"], digit_bits=best["digit_bits"],
+                            key_capacity=best["key_capacity"], device=dev)
+    g = b.capture(scene, tgt)
+    for _ in range(max(args.warmup, 3)):
+        g.replay()
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 20))
+    with ClockSampler(dev.index) as clk:
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            g.replay()
+        z.record()
+        torch.cuda.synchronize()
+    t_batch = a.elapsed_time(z) / 1e3 / steps
+    b.check_status()
+    pairs = b.key_count()
+    del g
+
+    # plain path: one renderer per view, forward + residual + backward per view
+    plain = []
+    for c, t in zip(cams, targets):
+        probe = render.Renderer(n, c["width"], c["height"], tile=16, digit_bits=9, key_capacity=3 * n, device=dev)
+        probe.forward(scene, c)
+        probe.check_status()
+        cap = int(math.ceil(probe.key_count() * 1.1 / 4096) * 4096) + 4096
+        del probe
+        r = render.Renderer(n, c["width"], c["height"], tile=16, digit_bits=9, key_capacity=cap, device=dev)
+        plain.append((r, c, t, torch.empty_like(t)))
+    torch.cuda.empty_cache()
+
+    def plain_step():
+        for r, c, t, d in plain:
+            r.forward(scene, c)
+            capi.ws_image_residual(t.numel(), r.image, t, d)
+            r.backward(scene, c, d)
+
+    for _ in range(2):
+        plain_step()
+    torch.cuda.synchronize()
+    psteps = max(2, min(args.steps, 5))
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(psteps):
+        plain_step()
+    z.record()
+    torch.cuda.synchronize()
+    t_plain = a.elapsed_time(z) / 1e3 / psteps
+    V = len(cams)
+    return {
+        "metric": "batched fwd+bwd views/s", "value": round(V / t_batch, 2), "unit": "views/s", "n_gpus": 1,
+        "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": round(t_batch * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded 64-cluster scene, 64 orbit views, random U[0,1) targets)",
+        "config": {"workload": "2,000,000 Gaussians x 64 views 320x240..1920x1080, fwd + L2 residual + bwd",
+                   "tile": best["tile"], "digit_bits": best["digit_bits"], "pairs": pairs,
+                   "autotune": best.get("table"), "autotune_cached": best.get("cached")},
+        "plain": {"value": round(V / t_plain, 2), "unit": "views/s", "ms_per_step": round(t_plain * 1e3, 3),
+                  "note": "64 per-view forward + residual + backward calls, per-view gradients not summed"},
+        "speedup_vs_plain": round(t_plain / t_batch, 3),
+        "clocks": clk.summary(),
+    }
 
 
 # ------------------------------------------------------------- reference
@@ -408,9 +548,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hd", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="hd", choices=sorted(WORKLOADS) + ["batch"])
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--digit-bits", type=int, default=8)
+    ap.add_argument("--digit-bits", type=int, default=9)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

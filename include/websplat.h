@@ -230,6 +230,55 @@ ws_status ws_rasterize_backward(int64_t n, const float *means, const float *log_
                                 float *d_log_scales, float *d_quats, float *d_opacity_logits,
                                 float *d_sh, void *workspace, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched views: up to ws_batch_max_views() cameras of one scene rendered
+ * (and differentiated) together. Every view's image is bit-identical to the
+ * single-view path; the batch reads the scene once instead of once per view.
+ * Per-(view, Gaussian) arrays are view-major: entry (v, g) at v * n + g, with
+ * the per-Gaussian layouts of the single-view calls (mean2d[V][n][4],
+ * conic[V][n][3], depth[V][n], rgb[V][n][3], rect[V][n][4],
+ * tiles_touched[V][n], offsets[V * n + 1]); opacity[n] is shared by all
+ * views. Tiles are numbered in one global grid: view v's tiles follow those
+ * of views 0..v-1, and the keys carry that global tile id (sort bits [0, 31 +
+ * ceil(log2 total tiles))). Images are packed: view v's H_v x W_v x 3 floats
+ * start after those of views 0..v-1 (likewise t_final and n_contrib).
+ * ranges has one [start, end) pair per global tile. The paper renders one
+ * view at a time; this batching has no counterpart there. cams is a host
+ * array of `views` cameras; cfg applies to every view. */
+int32_t ws_batch_max_views(void);
+size_t ws_batch_workspace_bytes(int64_t n, int32_t views, const ws_camera *cams, int64_t key_capacity,
+                                const ws_config *cfg);
+ws_status ws_preprocess_batch(int64_t n, const float *means, const float *log_scales, const float *quats,
+                              const float *opacity_logits, const float *sh, int32_t views,
+                              const ws_camera *cams, const ws_config *cfg, float *mean2d, float *conic,
+                              float *depth, float *rgb, float *opacity, uint16_t *rect,
+                              uint32_t *tiles_touched, void *stream);
+ws_status ws_cull_batch(int64_t n, int32_t views, const ws_camera *cams, const ws_config *cfg,
+                        const uint32_t *tiles_touched, const uint16_t *rect, const float *depth,
+                        uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t key_capacity,
+                        uint32_t *num_keys, void *workspace, void *stream);
+ws_status ws_rasterize_batch(const uint32_t *num_keys, const uint64_t *keys, const uint32_t *vals, int64_t n,
+                             const float *mean2d, const float *conic, const float *opacity, const float *rgb,
+                             int32_t views, const ws_camera *cams, const ws_config *cfg, uint32_t *ranges,
+                             float *image, float *t_final, uint32_t *n_contrib, void *stream);
+/* Gradients summed over the views, in view order (deterministic). */
+ws_status ws_rasterize_backward_batch(int64_t n, const float *means, const float *log_scales,
+                                      const float *quats, const float *sh, int32_t views,
+                                      const ws_camera *cams, const ws_config *cfg, const float *mean2d,
+                                      const float *conic, const float *rgb, const float *opacity,
+                                      const uint16_t *rect, const uint32_t *offsets,
+                                      const uint32_t *tiles_touched, const uint32_t *vals,
+                                      const uint32_t *ranges, const float *t_final,
+                                      const uint32_t *n_contrib, const float *d_image,
+                                      int64_t key_capacity, float *d_means, float *d_log_scales,
+                                      float *d_quats, float *d_opacity_logits, float *d_sh,
+                                      void *workspace, void *stream);
+
+/* d_image = image - target over `count` floats (device): the gradient of the
+ * L2 loss 1/2 ||image - target||^2 used by the training step. */
+ws_status ws_image_residual(int64_t count, const float *image, const float *target, float *d_image,
+                            void *stream);
+
 /* Reads (and, if clear != 0, clears) the device status word of a workspace:
  * waits for `stream`, then stores the WS_FLAG_* bits in *flags (host). This
  * is the one call that synchronises the host. */

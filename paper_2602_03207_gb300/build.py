@@ -1,7 +1,10 @@
 """Builds the sm_103a C-ABI library ``_build/libwebsplat.so`` in-tree with nvcc.
 
 Each translation unit is compiled in parallel (one -gencode, -O3, -lineinfo)
-and linked with ``nvcc -shared``. Rebuilds only when a source or header is
+and linked with ``nvcc -shared``. ``-fmad=false``: the compiler may not fuse a
+multiply and an add on its own (only explicit fmaf() calls are fused), so the
+device functions shared by the single-view and batched kernels round the same
+way wherever they are inlined and the two paths agree bit for bit. Rebuilds only when a source or header is
 newer than the library. Run ``python -m paper_2602_03207_gb300.build``.
 """
 from __future__ import annotations
@@ -20,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libwebsplat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 
 def _nvcc():

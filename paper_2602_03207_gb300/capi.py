@@ -26,7 +26,9 @@ WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL = 1, 2
 
 EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_preprocess", "ws_cull",
            "ws_sort", "ws_sort_noalloc", "ws_sort_noalloc_max_keys", "ws_rasterize",
-           "ws_rasterize_backward", "ws_read_status")
+           "ws_rasterize_backward", "ws_read_status", "ws_batch_max_views", "ws_batch_workspace_bytes",
+           "ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
+           "ws_image_residual")
 
 
 class WsError(RuntimeError):
@@ -91,6 +93,18 @@ def lib():
             L.ws_sort_noalloc.restype = I32
             L.ws_sort_noalloc_max_keys.restype = I64
             L.ws_read_status.argtypes = [P, C.POINTER(U32), I32, P]
+            L.ws_batch_max_views.restype = I32
+            L.ws_batch_workspace_bytes.argtypes = [I64, I32, cam_p, I64, cfg_p]
+            L.ws_batch_workspace_bytes.restype = C.c_size_t
+            L.ws_preprocess_batch.argtypes = [I64, P, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P, P, P, P]
+            L.ws_cull_batch.argtypes = [I64, I32, cam_p, cfg_p, P, P, P, P, P, P, I64, P, P, P]
+            L.ws_rasterize_batch.argtypes = [P, P, P, I64, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P]
+            L.ws_rasterize_backward_batch.argtypes = [I64, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P, P, P, P,
+                                                      P, P, P, P, I64, P, P, P, P, P, P, P]
+            L.ws_image_residual.argtypes = [I64, P, P, P, P]
+            for name in ("ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
+                         "ws_image_residual"):
+                getattr(L, name).restype = I32
             for name in ("ws_preprocess", "ws_cull", "ws_sort", "ws_rasterize", "ws_rasterize_backward",
                          "ws_read_status"):
                 getattr(L, name).restype = I32
@@ -188,3 +202,59 @@ def ws_read_status(workspace, clear=False, stream=None) -> int:
     _check("ws_read_status", lib().ws_read_status(_ptr(workspace), C.byref(flags), int(bool(clear)),
                                                   _stream(stream)))
     return int(flags.value)
+
+
+# ------------------------------------------------------------ batched views
+
+def camera_array(cams):
+    """ctypes array of ws_camera from a list of camera dicts."""
+    arr = (Camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera(c)
+    return arr
+
+
+def ws_batch_max_views() -> int:
+    return int(lib().ws_batch_max_views())
+
+
+def ws_batch_workspace_bytes(n, cams_arr, key_capacity, cfg) -> int:
+    return int(lib().ws_batch_workspace_bytes(int(n), len(cams_arr), cams_arr, int(key_capacity), C.byref(cfg)))
+
+
+def ws_preprocess_batch(n, means, log_scales, quats, opacity_logits, sh, cams_arr, cfg, mean2d, conic, depth, rgb,
+                        opacity, rect, tiles_touched, stream=None):
+    _check("ws_preprocess_batch", lib().ws_preprocess_batch(
+        int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh), len(cams_arr),
+        cams_arr, C.byref(cfg), _ptr(mean2d), _ptr(conic), _ptr(depth), _ptr(rgb), _ptr(opacity), _ptr(rect),
+        _ptr(tiles_touched), _stream(stream)))
+
+
+def ws_cull_batch(n, cams_arr, cfg, tiles_touched, rect, depth, offsets, keys, vals, key_capacity, num_keys,
+                  workspace, stream=None):
+    _check("ws_cull_batch", lib().ws_cull_batch(
+        int(n), len(cams_arr), cams_arr, C.byref(cfg), _ptr(tiles_touched), _ptr(rect), _ptr(depth), _ptr(offsets),
+        _ptr(keys), _ptr(vals), int(key_capacity), _ptr(num_keys), _ptr(workspace), _stream(stream)))
+
+
+def ws_rasterize_batch(num_keys, keys, vals, n, mean2d, conic, opacity, rgb, cams_arr, cfg, ranges, image, t_final,
+                       n_contrib, stream=None):
+    _check("ws_rasterize_batch", lib().ws_rasterize_batch(
+        _ptr(num_keys), _ptr(keys), _ptr(vals), int(n), _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb),
+        len(cams_arr), cams_arr, C.byref(cfg), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib),
+        _stream(stream)))
+
+
+def ws_rasterize_backward_batch(n, means, log_scales, quats, sh, cams_arr, cfg, mean2d, conic, rgb, opacity, rect,
+                                offsets, tiles_touched, vals, ranges, t_final, n_contrib, d_image, key_capacity,
+                                d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, workspace, stream=None):
+    _check("ws_rasterize_backward_batch", lib().ws_rasterize_backward_batch(
+        int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(sh), len(cams_arr), cams_arr, C.byref(cfg),
+        _ptr(mean2d), _ptr(conic), _ptr(rgb), _ptr(opacity), _ptr(rect), _ptr(offsets), _ptr(tiles_touched),
+        _ptr(vals), _ptr(ranges), _ptr(t_final), _ptr(n_contrib), _ptr(d_image), int(key_capacity), _ptr(d_means),
+        _ptr(d_log_scales), _ptr(d_quats), _ptr(d_opacity_logits), _ptr(d_sh), _ptr(workspace), _stream(stream)))
+
+
+def ws_image_residual(count, image, target, d_image, stream=None):
+    _check("ws_image_residual", lib().ws_image_residual(int(count), _ptr(image), _ptr(target), _ptr(d_image),
+                                                        _stream(stream)))

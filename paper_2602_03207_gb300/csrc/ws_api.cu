@@ -61,7 +61,7 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 // scratch]. The first three depend only on the key capacity (the sort region
 // is sized for the widest supported digit, so any digit width fits), so
 // ws_sort and ws_rasterize_backward find their regions without knowing n.
-constexpr int kMaxDigitBits = 8;
+constexpr int kMaxDigitBits = 11;
 
 struct Layout {
     size_t status, sort, bwd, cull, total;
@@ -78,6 +78,34 @@ Layout layout(int64_t n, int64_t cap) {
 }
 
 ws_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WS_OK : WS_ERR_CUDA; }
+
+// Host-side table of a batch's cameras: per-view frame constants and the
+// global tile / pixel numbering. Returns false for invalid arguments.
+bool make_table(int32_t views, const ws_camera* cams, const ws_config* cfg, ws::FrameTable& ft) {
+    if (views <= 0 || views > ws::kMaxViews || !cams || !valid_config(cfg)) return false;
+    ft.views = views;
+    ft.tile_off[0] = 0;
+    ft.pix_off[0] = 0;
+    for (int v = 0; v < views; ++v) {
+        if (!valid_camera(cams + v)) return false;
+        ft.f[v] = make_frame(cams + v, cfg);
+        if (ft.f[v].TX > 65535 || ft.f[v].TY > 65535) return false;
+        const uint64_t t = (uint64_t)ft.tile_off[v] + (uint64_t)ft.f[v].TX * ft.f[v].TY;
+        if (t >= (uint64_t(1) << 32)) return false;
+        ft.tile_off[v + 1] = (uint32_t)t;
+        ft.pix_off[v + 1] = ft.pix_off[v] + (uint64_t)cams[v].width * cams[v].height;
+    }
+    for (int v = views; v < ws::kMaxViews; ++v) ft.tile_off[v + 1] = ft.tile_off[views];
+    return true;
+}
+
+ws::ViewGrid make_grid(const ws::FrameTable& ft) {
+    ws::ViewGrid g;
+    g.views = ft.views;
+    for (int v = 0; v <= ws::kMaxViews; ++v) g.tile_off[v] = ft.tile_off[v];
+    for (int v = 0; v < ws::kMaxViews; ++v) g.tiles_x[v] = v < ft.views ? (uint32_t)ft.f[v].TX : 0u;
+    return g;
+}
 
 }  // namespace
 
@@ -142,8 +170,6 @@ ws_status ws_cull(int64_t n, const uint32_t* tiles_touched, const uint16_t* rect
     char* ws_base = static_cast<char*>(workspace);
     uint32_t* status = reinterpret_cast<uint32_t*>(ws_base + L.status);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(status, 0, ws::kStatusBytes, s);
-    if (e != cudaSuccess) return WS_ERR_CUDA;
     return cuda_status(ws::launch_cull(n, tiles_touched, rect, depth, f, offsets, keys, vals,
                                        key_capacity, num_keys, status, ws_base + L.cull, s));
 }
@@ -177,7 +203,7 @@ int64_t ws_sort_noalloc_max_keys(void) { return ws::sort_noalloc_max_keys(); }
 ws_status ws_sort_noalloc(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_bit, int32_t end_bit,
                           uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                           int32_t digit_bits, int32_t* result_in_alt, void* stream) {
-    if (!ws::sort_digit_supported(digit_bits)) return WS_ERR_UNSUPPORTED;
+    if (!ws::sort_digit_supported(digit_bits) || digit_bits > 8) return WS_ERR_UNSUPPORTED;
     if (key_capacity < 0 || key_capacity > ws::sort_noalloc_max_keys() || begin_bit < 0 || end_bit > 64 ||
         begin_bit >= end_bit || !result_in_alt)
         return WS_ERR_INVALID_ARG;
@@ -238,6 +264,108 @@ ws_status ws_rasterize_backward(int64_t n, const float* means, const float* log_
                                            d_image, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
                                            ws_base + layout(0, key_capacity).bwd,
                                            static_cast<cudaStream_t>(stream)));
+}
+
+size_t ws_batch_workspace_bytes(int64_t n, int32_t views, const ws_camera* cams, int64_t key_capacity,
+                                const ws_config* cfg) {
+    ws::FrameTable ft;
+    if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 31) || !make_table(views, cams, cfg, ft))
+        return 0;
+    if (!ws::sort_digit_supported(cfg->digit_bits) || n * views >= (int64_t(1) << 32)) return 0;
+    return layout(n * views, key_capacity).total;
+}
+
+int32_t ws_batch_max_views(void) { return ws::kMaxViews; }
+
+ws_status ws_preprocess_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
+                              const float* opacity_logits, const float* sh, int32_t views, const ws_camera* cams,
+                              const ws_config* cfg, float* mean2d, float* conic, float* depth, float* rgb,
+                              float* opacity, uint16_t* rect, uint32_t* tiles_touched, void* stream) {
+    ws::FrameTable ft;
+    if (n < 0 || !make_table(views, cams, cfg, ft) || n * views >= (int64_t(1) << 32)) return WS_ERR_INVALID_ARG;
+    if (n == 0) return WS_OK;
+    const void* ptrs[] = {means, log_scales, quats, opacity_logits, sh, mean2d, conic, depth,
+                          rgb, opacity, rect, tiles_touched};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    return cuda_status(ws::launch_preprocess_batch(n, means, log_scales, quats, opacity_logits, sh, ft, mean2d,
+                                                   conic, depth, rgb, opacity, rect, tiles_touched,
+                                                   static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_cull_batch(int64_t n, int32_t views, const ws_camera* cams, const ws_config* cfg,
+                        const uint32_t* tiles_touched, const uint16_t* rect, const float* depth, uint32_t* offsets,
+                        uint64_t* keys, uint32_t* vals, int64_t key_capacity, uint32_t* num_keys, void* workspace,
+                        void* stream) {
+    ws::FrameTable ft;
+    if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 31) || !make_table(views, cams, cfg, ft) ||
+        n * views >= (int64_t(1) << 32) || !ws::sort_digit_supported(cfg->digit_bits))
+        return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {offsets, num_keys, workspace};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (n > 0) {
+        const void* in[] = {tiles_touched, rect, depth};
+        for (const void* p : in)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    if (key_capacity > 0 && (!keys || !vals || !aligned16(keys) || !aligned16(vals))) return WS_ERR_INVALID_ARG;
+    const Layout L = layout(n * views, key_capacity);
+    char* ws_base = static_cast<char*>(workspace);
+    return cuda_status(ws::launch_cull_batch(n, make_grid(ft), tiles_touched, rect, depth, offsets, keys, vals,
+                                             key_capacity, num_keys, reinterpret_cast<uint32_t*>(ws_base + L.status),
+                                             ws_base + L.cull, static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_rasterize_batch(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals, int64_t n,
+                             const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                             int32_t views, const ws_camera* cams, const ws_config* cfg, uint32_t* ranges,
+                             float* image, float* t_final, uint32_t* n_contrib, void* stream) {
+    ws::FrameTable ft;
+    if (n < 0 || !make_table(views, cams, cfg, ft)) return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, keys, vals, mean2d, conic, opacity, rgb, ranges, image, t_final, n_contrib};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    return cuda_status(ws::launch_rasterize_batch(num_keys, keys, vals, n, mean2d, conic, opacity, rgb, ft, ranges,
+                                                  image, t_final, n_contrib, static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_rasterize_backward_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
+                                      const float* sh, int32_t views, const ws_camera* cams, const ws_config* cfg,
+                                      const float* mean2d, const float* conic, const float* rgb,
+                                      const float* opacity, const uint16_t* rect, const uint32_t* offsets,
+                                      const uint32_t* tiles_touched, const uint32_t* vals, const uint32_t* ranges,
+                                      const float* t_final, const uint32_t* n_contrib, const float* d_image,
+                                      int64_t key_capacity, float* d_means, float* d_log_scales, float* d_quats,
+                                      float* d_opacity_logits, float* d_sh, void* workspace, void* stream) {
+    ws::FrameTable ft;
+    if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 31) || !make_table(views, cams, cfg, ft))
+        return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {ranges, t_final, n_contrib, d_image, workspace, offsets};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (n > 0) {
+        const void* per[] = {means, log_scales, quats, sh, mean2d, conic, rgb, opacity, rect,
+                             tiles_touched, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
+        for (const void* p : per)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    if (key_capacity > 0 && (!vals || !aligned16(vals))) return WS_ERR_INVALID_ARG;
+    char* ws_base = static_cast<char*>(workspace);
+    return cuda_status(ws::launch_backward_batch(n, means, log_scales, quats, sh, ft, mean2d, conic, rgb, opacity,
+                                                 rect, offsets, tiles_touched, vals, ranges, t_final, n_contrib,
+                                                 d_image, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
+                                                 ws_base + layout(0, key_capacity).bwd,
+                                                 static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_image_residual(int64_t count, const float* image, const float* target, float* d_image, void* stream) {
+    if (count < 0) return WS_ERR_INVALID_ARG;
+    if (count == 0) return WS_OK;
+    const void* ptrs[] = {image, target, d_image};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    return cuda_status(ws::launch_residual(count, image, target, d_image, static_cast<cudaStream_t>(stream)));
 }
 
 ws_status ws_read_status(void* workspace, uint32_t* flags, int32_t clear, void* stream) {

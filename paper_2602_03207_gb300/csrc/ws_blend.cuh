@@ -1,0 +1,331 @@
+// Per-tile blend body (paper §3.4 with §2.1's compositing), shared by the
+// single-view and the batched rasterisation kernels.
+#pragma once
+
+#include "ws_common.cuh"
+
+namespace ws {
+
+constexpr int kBlendBatch = 256;
+
+// Shared-memory record of one splat for the blend (48 bytes).
+struct SplatRec {
+    float4 geo;   // tile-relative centre x, y; conic premultiplied A, B
+    float4 geo2;  // C, opacity, -, -
+    float4 col;   // r, g, b, -
+};
+
+// One block per tile. Each warp owns WPB (TS^2/256, at least 1) 8x4 pixel
+// blocks. Splats are staged 256 at a time; while staging, every splat also
+// records the bitmask of the tile's 8x4 blocks that its opacity-aware
+// extent box reaches. Each warp then walks the batch 32 splats at a time,
+// ballots the bit of its own block and visits only those splats, in list
+// order, so per pixel the compositing order is unchanged.
+template <int TS>
+__device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
+                                           const float4* __restrict__ mean2d, const float* __restrict__ conic,
+                                           const float* __restrict__ opacity, const float* __restrict__ rgb,
+                                           float* __restrict__ image, float* __restrict__ t_final,
+                                           uint32_t* __restrict__ n_contrib) {
+    constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
+    constexpr int WARPS = THREADS / 32;
+    constexpr int PPT = TS * TS / THREADS;  // pixel blocks per warp (TS = 32: 4)
+    constexpr int BW = 8, BH = 4;           // warp pixel block
+    constexpr int BPR = TS / BW;            // blocks per row
+    constexpr int BROWS = TS / BH;          // block rows
+    static_assert(BPR * BROWS <= 32, "block mask is 32 bits");
+    __shared__ SplatRec s_rec[kBlendBatch];
+    __shared__ uint32_t s_mask[kBlendBatch];
+
+    const int tx = tile % f.TX, ty = tile / f.TX;
+    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    float px[PPT], py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    uint32_t last[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int b = warp + k * WARPS;
+        const int bx = (b % BPR) * BW, by = (b / BPR) * BH;
+        px[k] = (float)(bx + (lane & 7)) + 0.5f;
+        py[k] = (float)(by + (lane >> 3)) + 0.5f;
+        T[k] = 1.f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        last[k] = 0;
+    }
+
+    for (uint32_t start = range.x; start < range.y; start += kBlendBatch) {
+        const int cnt = (int)min((uint32_t)kBlendBatch, range.y - start);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += THREADS) {
+            const uint32_t g = __ldg(vals + start + j);
+            const float4 m = __ldg(mean2d + g);
+            const float a = __ldg(conic + 3 * g), b = __ldg(conic + 3 * g + 1), c = __ldg(conic + 3 * g + 2);
+            const float op = __ldg(opacity + g);
+            SplatRec r;
+            r.geo.x = __fadd_rn(__fsub_rn(m.x, ox), m.z);
+            r.geo.y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
+            r.geo.z = -0.5f * kLog2e * a;
+            r.geo.w = -kLog2e * b;
+            r.geo2 = make_float4(-0.5f * kLog2e * c, op, 0.f, 0.f);
+            r.col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), 0.f);
+            s_rec[j] = r;
+            // Box of the ellipse where the alpha reaches 1/255 (§3.4), with a
+            // small margin so rounding never drops a pair the per-pixel test
+            // would keep: half-widths sqrt(q_c Sigma'_xx), sqrt(q_c Sigma'_yy).
+            const float det = fmaf(a, c, -b * b);
+            const float qc = fmaxf(0.f, 2.f * (kLn255 + __logf(op)));
+            const float ex = sqrtf(qc * c / det) * 1.0001f + 1e-3f;
+            const float ey = sqrtf(qc * a / det) * 1.0001f + 1e-3f;
+            // blocks whose pixel centres [8c + .5, 8c + 7.5] x [4r + .5, 4r + 3.5] meet the box
+            const float c0 = fmaxf(0.f, ceilf((r.geo.x - ex - (BW - 0.5f)) * (1.f / BW)));
+            const float c1 = fminf((float)(BPR - 1), floorf((r.geo.x + ex - 0.5f) * (1.f / BW)));
+            const float r0 = fmaxf(0.f, ceilf((r.geo.y - ey - (BH - 0.5f)) * (1.f / BH)));
+            const float r1 = fminf((float)(BROWS - 1), floorf((r.geo.y + ey - 0.5f) * (1.f / BH)));
+            uint32_t mask = 0;
+            if (c0 <= c1 && r0 <= r1) {
+                const int ic0 = (int)c0, ic1 = (int)c1, ir0 = (int)r0, ir1 = (int)r1;
+                const uint32_t row = ((2u << ic1) - 1u) & ~((1u << ic0) - 1u);
+                for (int rr = ir0; rr <= ir1; ++rr) mask |= row << (rr * BPR);
+            }
+            s_mask[j] = mask;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const int blk = warp + k * WARPS;
+            for (int base = 0; base < cnt; base += 32) {
+                const int jj = base + lane;
+                uint32_t bits = __ballot_sync(kFull, jj < cnt && ((s_mask[jj] >> blk) & 1u));
+                while (bits) {
+                    const int j = base + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const float4 geo = s_rec[j].geo;
+                    const float4 geo2 = s_rec[j].geo2;
+                    const float dx = px[k] - geo.x, dy = py[k] - geo.y;
+                    const float alpha = splat_alpha(dx, dy, geo.z, geo.w, geo2.x, geo2.y);
+                    if (alpha < kAlphaMin) continue;
+                    const float4 col = s_rec[j].col;
+                    const float w = alpha * T[k];
+                    C0[k] = fmaf(col.x, w, C0[k]);
+                    C1[k] = fmaf(col.y, w, C1[k]);
+                    C2[k] = fmaf(col.z, w, C2[k]);
+                    T[k] = T[k] - w;
+                    last[k] = start + j + 1 - range.x;
+                }
+            }
+        }
+    }
+
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int gx = tx * TS + (int)px[k], gy = ty * TS + (int)py[k];
+        if (gx < f.W && gy < f.H) {
+            const size_t pix = (size_t)gy * f.W + gx;
+            image[3 * pix] = fmaf(T[k], f.bg[0], C0[k]);
+            image[3 * pix + 1] = fmaf(T[k], f.bg[1], C1[k]);
+            image[3 * pix + 2] = fmaf(T[k], f.bg[2], C2[k]);
+            t_final[pix] = T[k];
+            n_contrib[pix] = last[k];
+        }
+    }
+}
+
+
+constexpr int kBwdBatch = 64;
+constexpr int kPart = 9;  // dmean x, y; dconic a, b, c; dsigma; drgb r, g, b
+
+struct BwdRec {
+    float4 geo;   // tile-relative centre x, y; premultiplied conic A, B
+    float4 geo2;  // premultiplied C, opacity, conic a, conic b
+    float4 col;   // r, g, b, conic c
+};
+
+// `tile` is the tile index within the frame; `slot_of(g)` gives the first
+// emission slot of Gaussian g's pairs for this frame (offsets[g] for one view,
+// offsets[g * views + v] in a batch).
+template <int TS, typename SlotBase>
+__device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
+                                               const float4* __restrict__ mean2d, const float* __restrict__ conic,
+                                               const float* __restrict__ opacity, const float* __restrict__ rgb,
+                                               const uint2* __restrict__ rect, SlotBase slot_of,
+                                               const float* __restrict__ t_final,
+                                               const uint32_t* __restrict__ n_contrib,
+                                               const float* __restrict__ d_image, float* __restrict__ partials) {
+    constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
+    constexpr int WARPS = THREADS / 32;
+    constexpr int PPT = TS * TS / THREADS;
+    constexpr int BW = 8, BH = 4;
+    constexpr int BPR = TS / BW;
+    constexpr int BROWS = TS / BH;
+    __shared__ BwdRec s_rec[kBwdBatch];
+    __shared__ uint32_t s_mask[kBwdBatch];
+    __shared__ uint32_t s_slot[kBwdBatch];
+    __shared__ float s_part[kBwdBatch][WARPS][kPart];
+    __shared__ uint32_t s_max[WARPS];
+
+    const int tx = tile % f.TX, ty = tile / f.TX;
+    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t len = range.y - range.x;
+
+    float px[PPT], py[PPT], T[PPT], dC[PPT][3], Bc[PPT][3];
+    uint32_t last[PPT];
+    uint32_t wmask = 0;  // union of this warp's block bits
+    uint32_t my_max = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int b = warp + k * WARPS;
+        wmask |= 1u << b;
+        const int bx = (b % BPR) * BW, by = (b / BPR) * BH;
+        const int lx = bx + (lane & 7), ly = by + (lane >> 3);
+        px[k] = (float)lx + 0.5f;
+        py[k] = (float)ly + 0.5f;
+        const int gx = tx * TS + lx, gy = ty * TS + ly;
+        const bool inside = gx < f.W && gy < f.H;
+        const size_t pix = inside ? (size_t)gy * f.W + gx : 0;
+        T[k] = inside ? t_final[pix] : 1.f;
+        last[k] = inside ? n_contrib[pix] : 0u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dC[k][c] = inside ? d_image[3 * pix + c] : 0.f;
+            Bc[k][c] = f.bg[c];
+        }
+        my_max = max(my_max, last[k]);
+    }
+    // Block-wide maximum of the last-contributor counts: positions past it
+    // are never composited, their records are zero.
+    for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(kFull, my_max, o));
+    if (lane == 0) s_max[warp] = my_max;
+    __syncthreads();
+    uint32_t max_last = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) max_last = max(max_last, s_max[w]);
+
+    // Zero records for list positions no pixel composited.
+    for (uint32_t j = max_last + threadIdx.x; j < len; j += THREADS) {
+        const uint32_t g = __ldg(vals + range.x + j);
+        const uint2 r = __ldg(rect + g);
+        const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
+        const uint32_t slot = slot_of(g) + (ty - y0) * (x1 - x0 + 1) + (tx - x0);
+        float* dst = partials + (size_t)slot * kPart;
+#pragma unroll
+        for (int c = 0; c < kPart; ++c) dst[c] = 0.f;
+    }
+
+    for (int end = (int)max_last; end > 0; end -= kBwdBatch) {
+        const int lo = max(0, end - kBwdBatch);
+        const int cnt = end - lo;
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += THREADS) {
+            const uint32_t g = __ldg(vals + range.x + lo + j);
+            const float4 m = __ldg(mean2d + g);
+            const float a = __ldg(conic + 3 * g), b = __ldg(conic + 3 * g + 1), c = __ldg(conic + 3 * g + 2);
+            const float op = __ldg(opacity + g);
+            BwdRec r;
+            r.geo.x = __fadd_rn(__fsub_rn(m.x, ox), m.z);
+            r.geo.y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
+            r.geo.z = -0.5f * kLog2e * a;
+            r.geo.w = -kLog2e * b;
+            r.geo2 = make_float4(-0.5f * kLog2e * c, op, a, b);
+            r.col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), c);
+            s_rec[j] = r;
+            const float det = fmaf(a, c, -b * b);
+            const float qc = fmaxf(0.f, 2.f * (kLn255 + __logf(op)));
+            const float ex = sqrtf(qc * c / det) * 1.0001f + 1e-3f;
+            const float ey = sqrtf(qc * a / det) * 1.0001f + 1e-3f;
+            const float c0 = fmaxf(0.f, ceilf((r.geo.x - ex - (BW - 0.5f)) * (1.f / BW)));
+            const float c1 = fminf((float)(BPR - 1), floorf((r.geo.x + ex - 0.5f) * (1.f / BW)));
+            const float r0 = fmaxf(0.f, ceilf((r.geo.y - ey - (BH - 0.5f)) * (1.f / BH)));
+            const float r1 = fminf((float)(BROWS - 1), floorf((r.geo.y + ey - 0.5f) * (1.f / BH)));
+            uint32_t mask = 0;
+            if (c0 <= c1 && r0 <= r1) {
+                const int ic0 = (int)c0, ic1 = (int)c1, ir0 = (int)r0, ir1 = (int)r1;
+                const uint32_t row = ((2u << ic1) - 1u) & ~((1u << ic0) - 1u);
+                for (int rr = ir0; rr <= ir1; ++rr) mask |= row << (rr * BPR);
+            }
+            s_mask[j] = mask;
+            const uint2 rc = __ldg(rect + g);
+            const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+            s_slot[j] = slot_of(g) + (ty - y0) * (x1 - x0 + 1) + (tx - x0);
+        }
+        for (int e = threadIdx.x; e < cnt * WARPS * kPart; e += THREADS) (&s_part[0][0][0])[e] = 0.f;
+        __syncthreads();
+
+        // Back to front over the batch: chunks of 32 from the top, highest
+        // set bit first.
+        for (int base = ((cnt - 1) >> 5) << 5; base >= 0; base -= 32) {
+            const int jj = base + lane;
+            uint32_t bits = __ballot_sync(kFull, jj < cnt && (s_mask[jj] & wmask) != 0u);
+            while (bits) {
+                const int hb = 31 - __clz(bits);
+                bits &= ~(1u << hb);
+                const int j = base + hb;
+                const uint32_t pos = (uint32_t)(lo + j);
+                const BwdRec r = s_rec[j];
+                const uint32_t m = s_mask[j];
+                float acc[kPart];
+#pragma unroll
+                for (int c = 0; c < kPart; ++c) acc[c] = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (!((m >> (warp + k * WARPS)) & 1u)) continue;  // warp-uniform
+                    if (pos >= last[k]) continue;
+                    const float dx = px[k] - r.geo.x, dy = py[k] - r.geo.y;
+                    const float G = ex2_approx(splat_power2(dx, dy, r.geo.z, r.geo.w, r.geo2.x));
+                    const float raw = __fmul_rn(r.geo2.y, G);
+                    const float alpha = fminf(kAlphaMax, raw);
+                    if (alpha < kAlphaMin) continue;
+                    any = true;
+                    const float Tb = T[k] / (1.f - alpha);
+                    const float w = alpha * Tb;
+                    float dalpha = 0.f;
+                    const float cc[3] = {r.col.x, r.col.y, r.col.z};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        acc[6 + c] = fmaf(w, dC[k][c], acc[6 + c]);
+                        dalpha = fmaf(cc[c] - Bc[k][c], dC[k][c], dalpha);
+                        Bc[k][c] = fmaf(alpha, cc[c] - Bc[k][c], Bc[k][c]);
+                    }
+                    dalpha *= Tb;
+                    T[k] = Tb;
+                    if (raw < kAlphaMax) {
+                        acc[5] = fmaf(G, dalpha, acc[5]);
+                        const float dp = alpha * dalpha;
+                        const float ca = r.geo2.z, cb = r.geo2.w, cc2 = r.col.w;
+                        acc[0] = fmaf(dp, ca * dx + cb * dy, acc[0]);
+                        acc[1] = fmaf(dp, cb * dx + cc2 * dy, acc[1]);
+                        acc[2] = fmaf(dp, -0.5f * dx * dx, acc[2]);
+                        acc[3] = fmaf(dp, -dx * dy, acc[3]);
+                        acc[4] = fmaf(dp, -0.5f * dy * dy, acc[4]);
+                    }
+                }
+                if (__any_sync(kFull, any)) {
+#pragma unroll
+                    for (int c = 0; c < kPart; ++c) {
+                        float v = acc[c];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                        acc[c] = v;
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int c = 0; c < kPart; ++c) s_part[j][warp][c] = acc[c];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // Block sum over warps in warp order, one record per pair.
+        for (int e = threadIdx.x; e < cnt * kPart; e += THREADS) {
+            const int j = e / kPart, c = e - j * kPart;
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) s += s_part[j][w][c];
+            partials[(size_t)s_slot[j] * kPart + c] = s;
+        }
+    }
+}
+
+}  // namespace ws

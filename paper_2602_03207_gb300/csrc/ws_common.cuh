@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "websplat.h"
@@ -29,6 +30,35 @@ struct Frame {
     int TS, TX, TY;   // tile side and tile grid
     uint32_t flags;
 };
+
+// Several cameras of one scene rendered as one batch (at most kMaxViews).
+// Per-(view, Gaussian) arrays are view-major: element (v, g) is at v * n + g.
+// View v's tiles are numbered tile_off[v] .. tile_off[v+1]-1 in one global
+// tile grid and its pixels start at pix_off[v] in the packed image.
+constexpr int kMaxViews = 64;
+
+struct ViewGrid {
+    uint32_t tiles_x[kMaxViews];
+    uint32_t tile_off[kMaxViews + 1];
+    int views;
+};
+
+struct FrameTable {
+    Frame f[kMaxViews];
+    uint32_t tile_off[kMaxViews + 1];
+    uint64_t pix_off[kMaxViews + 1];
+    int views;
+};
+
+// The view owning global tile t (binary search over tile_off).
+__device__ __forceinline__ int view_of_tile(const uint32_t* tile_off, int views, uint32_t t) {
+    int lo = 0, hi = views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // ---------------------------------------------------------------------------
 // Double-float ("unevaluated sum of two floats") arithmetic. Error-free
@@ -159,6 +189,33 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
     *total = smem[THREADS / 32];
     __syncthreads();
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch. Every kernel of the path is launched with
+// programmatic stream serialisation, so it may be scheduled while its
+// predecessor in the stream drains; it calls pdl_wait() before its first
+// global-memory access (read or write), which returns once the predecessor
+// grid has completed and its writes are visible, and pdl_trigger() to let its
+// own successor launch early. Launch latency overlaps the predecessor's tail;
+// ordering and results are those of plain stream order.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 __device__ __forceinline__ void set_flag(uint32_t* status, uint32_t bit) {

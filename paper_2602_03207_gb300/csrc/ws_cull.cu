@@ -30,6 +30,8 @@ constexpr int kTopThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads)
 k_chunk_sums(int64_t n, const uint32_t* __restrict__ touched, uint32_t* __restrict__ sums) {
     __shared__ uint32_t s_red[kScanThreads / 32 + 1];
+    pdl_wait();
+    pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * kChunk;
     uint32_t acc = 0;
 #pragma unroll
@@ -48,6 +50,8 @@ __global__ void __launch_bounds__(kTopThreads)
 k_chunk_scan(int64_t nchunks, int64_t n, uint32_t* __restrict__ sums, uint32_t* __restrict__ offsets,
              uint32_t* __restrict__ num_keys, int64_t capacity, uint32_t* __restrict__ status) {
     __shared__ uint32_t s_red[kTopThreads / 32 + 1];
+    pdl_wait();
+    pdl_trigger();
     uint32_t carry = 0;
     for (int64_t start = 0; start < nchunks; start += kTopThreads) {
         int64_t c = start + threadIdx.x;
@@ -59,22 +63,30 @@ k_chunk_scan(int64_t nchunks, int64_t n, uint32_t* __restrict__ sums, uint32_t* 
     }
     if (threadIdx.x == 0) {
         offsets[n] = carry;
-        uint32_t k = (int64_t)carry > capacity ? (uint32_t)capacity : carry;
-        *num_keys = k;
-        if ((int64_t)carry > capacity) set_flag(status, WS_FLAG_CAPACITY);
+        const bool over = (int64_t)carry > capacity;
+        *num_keys = over ? (uint32_t)capacity : carry;
+        // This frame's status words: stored outright, so no clear is needed.
+        status[0] = over ? 1u : 0u;
+        status[1] = 0u;
     }
 }
 
-// Level 0 down + emission.
+// Level 0 down + emission. In a batch (BATCH = true) item i is (view
+// v = i / per_view, Gaussian g = i - v * per_view), its tile ids are offset
+// into the global tile grid and its value is g; for one view the item is
+// the Gaussian itself.
+template <bool BATCH>
 __global__ void __launch_bounds__(kScanThreads)
 k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
        const float* __restrict__ depth, const uint32_t* __restrict__ chunk_off, int tiles_x,
        uint32_t* __restrict__ offsets, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
-       int64_t capacity) {
+       int64_t capacity, uint32_t per_view, const ViewGrid grid) {
     __shared__ uint32_t s_off[kChunk + 1];
     __shared__ uint2 s_rect[kChunk];
     __shared__ uint32_t s_depth[kChunk];
     __shared__ uint32_t s_red[kScanThreads / 32 + 1];
+    pdl_wait();
+    pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * kChunk;
     const int cnt = (int)((n - base) < kChunk ? (n - base) : kChunk);
 
@@ -120,9 +132,19 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
         uint32_t rx0 = r.x & 0xffffu, ry0 = r.x >> 16, rx1 = r.y & 0xffffu;
         uint32_t w = rx1 - rx0 + 1;
         uint32_t dy = j / w, dx = j - dy * w;
-        uint64_t tile = (uint64_t)(ry0 + dy) * (uint64_t)tiles_x + (rx0 + dx);
+        const uint32_t item = (uint32_t)(base + lo);
+        uint64_t tile;
+        uint32_t val;
+        if (BATCH) {
+            const uint32_t v = item / per_view;
+            tile = (uint64_t)grid.tile_off[v] + (uint64_t)(ry0 + dy) * grid.tiles_x[v] + (rx0 + dx);
+            val = item - v * per_view;
+        } else {
+            tile = (uint64_t)(ry0 + dy) * (uint64_t)tiles_x + (rx0 + dx);
+            val = item;
+        }
         keys[slot] = (tile << 31) | (uint64_t)(s_depth[lo] & 0x7fffffffu);
-        vals[slot] = (uint32_t)(base + lo);
+        vals[slot] = val;
     }
 }
 
@@ -139,17 +161,49 @@ cudaError_t launch_cull(int64_t n, const uint32_t* tiles_touched, const uint16_t
                         uint32_t* status, void* scratch, cudaStream_t stream) {
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
     uint32_t* sums = static_cast<uint32_t*>(scratch);
+    cudaError_t e = cudaSuccess;
     if (nchunks > 0) {
-        k_chunk_sums<<<(unsigned)nchunks, kScanThreads, 0, stream>>>(n, tiles_touched, sums);
+        e = launch_pdl(k_chunk_sums, dim3((unsigned)nchunks), dim3(kScanThreads), 0, stream, n, tiles_touched, sums);
+        if (e != cudaSuccess) return e;
     }
-    k_chunk_scan<<<1, kTopThreads, 0, stream>>>(nchunks, n, sums, offsets, num_keys, key_capacity,
-                                               status);
+    e = launch_pdl(k_chunk_scan, dim3(1), dim3(kTopThreads), 0, stream, (int64_t)nchunks, n, sums, offsets,
+                   num_keys, key_capacity, status);
+    if (e != cudaSuccess) return e;
     if (nchunks > 0) {
-        k_emit<<<(unsigned)nchunks, kScanThreads, 0, stream>>>(
-            n, tiles_touched, reinterpret_cast<const uint2*>(rect), depth, sums, f.TX, offsets,
-            keys, vals, key_capacity);
+        ViewGrid g;
+        g.views = 1;
+        g.tiles_x[0] = (uint32_t)f.TX;
+        g.tile_off[0] = 0;
+        g.tile_off[1] = (uint32_t)(f.TX * f.TY);
+        e = launch_pdl(k_emit<false>, dim3((unsigned)nchunks), dim3(kScanThreads), 0, stream, n, tiles_touched,
+                       reinterpret_cast<const uint2*>(rect), depth, (const uint32_t*)sums, (int)f.TX, offsets,
+                       keys, vals, key_capacity, (uint32_t)(n > 0 ? n : 1), g);
     }
-    return cudaGetLastError();
+    return e;
+}
+
+cudaError_t launch_cull_batch(int64_t n, const ViewGrid& grid, const uint32_t* tiles_touched,
+                              const uint16_t* rect, const float* depth, uint32_t* offsets, uint64_t* keys,
+                              uint32_t* vals, int64_t key_capacity, uint32_t* num_keys, uint32_t* status,
+                              void* scratch, cudaStream_t stream) {
+    const int64_t items = n * grid.views;
+    const int64_t nchunks = (items + kChunk - 1) / kChunk;
+    uint32_t* sums = static_cast<uint32_t*>(scratch);
+    cudaError_t e = cudaSuccess;
+    if (nchunks > 0) {
+        e = launch_pdl(k_chunk_sums, dim3((unsigned)nchunks), dim3(kScanThreads), 0, stream, items, tiles_touched,
+                       sums);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_pdl(k_chunk_scan, dim3(1), dim3(kTopThreads), 0, stream, (int64_t)nchunks, items, sums, offsets,
+                   num_keys, key_capacity, status);
+    if (e != cudaSuccess) return e;
+    if (nchunks > 0) {
+        e = launch_pdl(k_emit<true>, dim3((unsigned)nchunks), dim3(kScanThreads), 0, stream, items, tiles_touched,
+                       reinterpret_cast<const uint2*>(rect), depth, (const uint32_t*)sums, 0, offsets, keys, vals,
+                       key_capacity, (uint32_t)n, grid);
+    }
+    return e;
 }
 
 }  // namespace ws

@@ -22,6 +22,11 @@ cudaError_t launch_cull(int64_t n, const uint32_t* tiles_touched, const uint16_t
                         uint32_t* vals, int64_t key_capacity, uint32_t* num_keys,
                         uint32_t* status, void* scratch, cudaStream_t stream);
 
+cudaError_t launch_cull_batch(int64_t n, const ViewGrid& grid, const uint32_t* tiles_touched,
+                              const uint16_t* rect, const float* depth, uint32_t* offsets, uint64_t* keys,
+                              uint32_t* vals, int64_t key_capacity, uint32_t* num_keys, uint32_t* status,
+                              void* scratch, cudaStream_t stream);
+
 // ---- radix sort
 size_t sort_scratch_bytes(int64_t key_capacity, int digit_bits);
 bool sort_digit_supported(int digit_bits);
@@ -39,6 +44,8 @@ cudaError_t launch_sort_noalloc(const uint32_t* num_keys, int64_t key_capacity, 
                                 cudaStream_t stream);
 
 // ---- rasterisation
+cudaError_t launch_tile_ranges(const uint64_t* keys, const uint32_t* num_keys, uint32_t* ranges, uint32_t ntiles,
+                               cudaStream_t stream);
 cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t key_capacity_hint,
                              const uint64_t* keys, const uint32_t* vals, const float* mean2d,
                              const float* conic, const float* opacity, const float* rgb,
@@ -55,5 +62,24 @@ cudaError_t launch_backward(int64_t n, const float* means, const float* log_scal
                             const uint32_t* n_contrib, const float* d_image, float* d_means,
                             float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
                             void* scratch, cudaStream_t stream);
+
+// ---- batched views (view-major per-(view, Gaussian) arrays)
+cudaError_t launch_preprocess_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
+                                    const float* logits, const float* sh, const FrameTable& ft, float* mean2d,
+                                    float* conic, float* depth, float* rgb, float* opacity, uint16_t* rect,
+                                    uint32_t* tiles_touched, cudaStream_t stream);
+cudaError_t launch_rasterize_batch(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals, int64_t n,
+                                   const float* mean2d, const float* conic, const float* opacity, const float* rgb,
+                                   const FrameTable& ft, uint32_t* ranges, float* image, float* t_final,
+                                   uint32_t* n_contrib, cudaStream_t stream);
+cudaError_t launch_backward_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
+                                  const float* sh, const FrameTable& ft, const float* mean2d, const float* conic,
+                                  const float* rgb, const float* opacity, const uint16_t* rect,
+                                  const uint32_t* offsets, const uint32_t* tiles_touched, const uint32_t* vals,
+                                  const uint32_t* ranges, const float* t_final, const uint32_t* n_contrib,
+                                  const float* d_image, float* d_means, float* d_log_scales, float* d_quats,
+                                  float* d_logits, float* d_sh, void* scratch, cudaStream_t stream);
+cudaError_t launch_residual(int64_t count, const float* image, const float* target, float* d_image,
+                            cudaStream_t stream);
 
 }  // namespace ws

@@ -7,8 +7,8 @@
 // is kept exactly. Each pass is three dispatches:
 //   1. upsweep:   every block counts the digits of its tile of keys
 //                 (warp-private histograms in shared memory, warp-aggregated
-//                 with match.any so heavily repeated digits cost one update
-//                 per warp instruction) and writes one column of the
+//                 by a per-bit ballot match, so each distinct digit costs one
+//                 update per warp instruction) and writes one column of the
 //                 digit-major matrix hist[d][tile].
 //   2. scan:      one block per digit scans its row; the exclusive row
 //                 prefix is prefix_wg, the row total feeds base_d.
@@ -35,7 +35,10 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / kWarp;
-constexpr int kSortItems = 16;
+#ifndef WS_SORT_ITEMS
+#define WS_SORT_ITEMS 8
+#endif
+constexpr int kSortItems = WS_SORT_ITEMS;  // keys per thread
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per block
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -44,17 +47,36 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Lanes of the warp holding the same BITS-bit digit as this lane: one ballot
+// per bit (inverted where this lane's bit is 0), ANDed together. Its cost does
+// not depend on how many distinct digits the warp holds. Lanes passing
+// `valid` = false take part in the votes but match no valid lane.
+template <int BITS>
+__device__ __forceinline__ uint32_t warp_match_digit(uint32_t digit, bool valid) {
+    uint32_t peers = __ballot_sync(kFull, valid);
+    if (!valid) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (digit >> b) & 1u;
+        const uint32_t vote = __ballot_sync(kFull, bit);
+        peers &= bit ? vote : ~vote;
+    }
+    return peers;
+}
+
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_upsweep(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, int shift,
                uint32_t mask, uint32_t* __restrict__ hist, int max_tiles) {
     constexpr int R = 1 << BITS;
-    __shared__ uint32_t s_hist[kSortWarps][R];
+    __shared__ uint16_t s_hist[kSortWarps][R];  // per-warp counts (<= 512 each)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_hist[0][0])[d] = 0;
+    pdl_wait();
+    pdl_trigger();
     const uint32_t n = *num_keys;
     const int tile = blockIdx.x;
     if ((int64_t)tile * kSortTile >= (int64_t)n) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_hist[0][0])[d] = 0;
     __syncthreads();
     const int64_t base = (int64_t)tile * kSortTile + warp * (kWarp * kSortItems);
     uint32_t dig[kSortItems];
@@ -65,8 +87,10 @@ k_sort_upsweep(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n
     }
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        uint32_t peers = __match_any_sync(kFull, dig[k]);
-        if (dig[k] < (uint32_t)R && lane == __ffs(peers) - 1) s_hist[warp][dig[k]] += __popc(peers);
+        const bool ok = dig[k] < (uint32_t)R;
+        const uint32_t peers = warp_match_digit<BITS>(dig[k], ok);
+        if (ok && lane == __ffs(peers) - 1)
+            s_hist[warp][dig[k]] = (uint16_t)(s_hist[warp][dig[k]] + __popc(peers));
         __syncwarp();
     }
     __syncthreads();
@@ -84,6 +108,8 @@ __global__ void __launch_bounds__(kSortThreads)
 k_sort_scan(const uint32_t* __restrict__ num_keys, uint32_t* __restrict__ hist,
             uint32_t* __restrict__ totals, int max_tiles) {
     __shared__ uint32_t s_red[kSortThreads / 32 + 1];
+    pdl_wait();
+    pdl_trigger();
     const uint32_t n = *num_keys;
     const int tiles = (int)((n + kSortTile - 1) / kSortTile);
     uint32_t* row = hist + (size_t)blockIdx.x * max_tiles;
@@ -128,14 +154,24 @@ k_sort_downsweep(const uint64_t* __restrict__ keys_in, const uint32_t* __restric
     uint32_t* s_goff = s_start + R;  // [R] global position of each run minus its local start
     uint32_t* s_red = s_goff + R;    // [warps + 1]
 
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_wh[0][0])[d] = 0;
+    pdl_wait();
+    pdl_trigger();
     const uint32_t n = *num_keys;
     const int tile = blockIdx.x;
     const int64_t tile_base = (int64_t)tile * kSortTile;
     if (tile_base >= (int64_t)n) return;
     const int count = (int)(((int64_t)n - tile_base) < kSortTile ? ((int64_t)n - tile_base) : kSortTile);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_wh[0][0])[d] = 0;
+    // Request this block's column of prefix_wg and the digit totals now, so
+    // their latency overlaps the key loads and the ranking below.
+    uint32_t tv[kPerThread], hv[kPerThread];
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        const int d = threadIdx.x * kPerThread + j;
+        tv[j] = d < R ? __ldg(totals + d) : 0u;
+        hv[j] = d < R ? __ldg(hist + (size_t)d * max_tiles + tile) : 0u;
+    }
     __syncthreads();
 
     // Load in warp-striped order: item k of lane l of warp w is element
@@ -157,14 +193,15 @@ k_sort_downsweep(const uint64_t* __restrict__ keys_in, const uint32_t* __restric
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        uint32_t d = dig[k];
-        uint32_t peers = __match_any_sync(kFull, d);
-        int leader = __ffs(peers) - 1;
+        const uint32_t d = dig[k];
+        const bool ok = d < (uint32_t)R;
+        const uint32_t peers = warp_match_digit<BITS>(d, ok);
+        const int leader = __ffs(peers) - 1;
         uint32_t prior = 0;
-        if (lane == leader && d < (uint32_t)R) prior = s_wh[warp][d];
+        if (lane == leader && ok) prior = s_wh[warp][d];
         prior = __shfl_sync(kFull, prior, leader);
         rnk[k] = (uint16_t)(prior + __popc(peers & lt));
-        if (lane == leader && d < (uint32_t)R) s_wh[warp][d] = (uint16_t)(prior + __popc(peers));
+        if (lane == leader && ok) s_wh[warp][d] = (uint16_t)(prior + __popc(peers));
         __syncwarp();
     }
     __syncthreads();
@@ -192,20 +229,15 @@ k_sort_downsweep(const uint64_t* __restrict__ keys_in, const uint32_t* __restric
     uint32_t ex = block_exclusive_scan<kSortThreads>(acc, s_red, &dummy);
     // base_d: exclusive scan of the digit totals of the whole pass.
     uint32_t tacc = 0;
-    uint32_t tv[kPerThread];
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        int d = threadIdx.x * kPerThread + j;
-        tv[j] = d < R ? totals[d] : 0u;
-        tacc += tv[j];
-    }
+    for (int j = 0; j < kPerThread; ++j) tacc += tv[j];
     uint32_t tex = block_exclusive_scan<kSortThreads>(tacc, s_red, &dummy);
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         int d = threadIdx.x * kPerThread + j;
         if (d < R) {
             s_start[d] = ex;
-            s_goff[d] = tex + hist[(size_t)d * max_tiles + tile] - ex;
+            s_goff[d] = tex + hv[j] - ex;
         }
         ex += cnt[j];
         tex += tv[j];
@@ -274,11 +306,16 @@ cudaError_t sort_passes(const uint32_t* num_keys, int64_t capacity, int begin_bi
         const int bits = end_bit - shift < BITS ? end_bit - shift : BITS;
         const uint32_t mask = (1u << bits) - 1u;
         if (max_tiles > 0) {
-            k_sort_upsweep<BITS><<<max_tiles, kSortThreads, 0, stream>>>(kin, num_keys, shift, mask,
-                                                                       s.hist, max_tiles);
-            k_sort_scan<<<1 << BITS, kSortThreads, 0, stream>>>(num_keys, s.hist, s.totals, max_tiles);
-            k_sort_downsweep<BITS><<<max_tiles, kSortThreads, smem, stream>>>(
-                kin, vin, kout, vout, num_keys, shift, mask, s.hist, s.totals, max_tiles);
+            e = launch_pdl(k_sort_upsweep<BITS>, dim3(max_tiles), dim3(kSortThreads), 0, stream,
+                           (const uint64_t*)kin, num_keys, shift, mask, s.hist, max_tiles);
+            if (e != cudaSuccess) return e;
+            e = launch_pdl(k_sort_scan, dim3(1 << BITS), dim3(kSortThreads), 0, stream, num_keys, s.hist,
+                           s.totals, max_tiles);
+            if (e != cudaSuccess) return e;
+            e = launch_pdl(k_sort_downsweep<BITS>, dim3(max_tiles), dim3(kSortThreads), smem, stream,
+                           (const uint64_t*)kin, (const uint32_t*)vin, kout, vout, num_keys, shift, mask,
+                           (const uint32_t*)s.hist, (const uint32_t*)s.totals, max_tiles);
+            if (e != cudaSuccess) return e;
         }
         uint64_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
@@ -290,7 +327,7 @@ cudaError_t sort_passes(const uint32_t* num_keys, int64_t capacity, int begin_bi
 
 }  // namespace
 
-bool sort_digit_supported(int digit_bits) { return digit_bits >= 4 && digit_bits <= 8; }
+bool sort_digit_supported(int digit_bits) { return digit_bits >= 4 && digit_bits <= 11; }
 
 size_t sort_scratch_bytes(int64_t key_capacity, int digit_bits) {
     const size_t R = (size_t)1 << digit_bits;
@@ -313,6 +350,9 @@ cudaError_t launch_sort(const uint32_t* num_keys, int64_t key_capacity, int begi
         case 6: return sort_passes<6>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
         case 7: return sort_passes<7>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
         case 8: return sort_passes<8>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 9: return sort_passes<9>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 10: return sort_passes<10>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
+        case 11: return sort_passes<11>(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, s, in_alt, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -101,7 +101,7 @@ def test_digit_widths_give_identical_frames():
     """The sort's digit width changes the pass structure, never the result."""
     scene, cam = S.small_forward()
     imgs = []
-    for bits in (4, 5, 6, 7, 8):
+    for bits in (4, 5, 6, 7, 8, 9, 10, 11):
         g = fetch(gpu_frame(scene, cam, digit_bits=bits))
         imgs.append((g["image"], g["sorted_keys"], g["sorted_vals"]))
     for im, k, v in imgs[1:]:

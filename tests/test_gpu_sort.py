@@ -56,7 +56,7 @@ def test_sort_matches_stable_sort(n, kind):
     np.testing.assert_array_equal(v, ev)
 
 
-@pytest.mark.parametrize("bits", [4, 5, 6, 7, 8])
+@pytest.mark.parametrize("bits", [4, 5, 6, 7, 8, 9, 10, 11])
 def test_digit_widths_and_partial_bit_ranges(bits):
     """Digit widths that do not divide the bit range (a short last pass)
     and a begin bit above 0 (low bits then keep their input order)."""
