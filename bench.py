@@ -32,6 +32,10 @@ WORKLOADS = {
     "uhd": {"desc": "6,000,000 Gaussians, 3840x2160, SH3, 8 orbit poses", "n": 6_000_000},
 }
 METRIC = "1080p frames/s at 1M splats"
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernel on the hd workload (profiles/kernels_hd_1080p_1M.md); to be reset
+# to None whenever that kernel changes.
+KERNEL_TRAFFIC = {("k_blend", 16): 51_511_808 + 16_859_648}
 STAGES = ("preprocess", "cull", "sort", "rasterize")
 
 
@@ -377,15 +381,14 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
     stages["rasterize"] = {"ms": round(ms, 4), "bound": "alu", "alg_evals": int(evals),
                            "achieved_tflops": round(ach, 3), "peak_tflops": round(peak_tflops, 2),
                            "frac": round(ach / peak_tflops, 4)}
-    dom = max(STAGES, key=lambda s: stage_ms[s])
-    d = stages[dom]
-    if d["bound"] == "hbm":
-        roof = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": d["frac"], "traffic": None, "peak_source": peaks["source"]}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": d["achieved_tflops"], "peak": d["peak_tflops"],
-                "unit": "TFLOP/s", "frac": d["frac"], "traffic": None,
-                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"}
+    # The dominant single kernel of a frame is k_blend (largest share of the
+    # ncu launch list). Its timed span is the ws_rasterize call, which also
+    # holds the two small tile-range kernels, so the fraction is conservative.
+    d = stages["rasterize"]
+    roof = {"kernel": "k_blend<%d> (timed span: ws_rasterize)" % r.tile, "bound": "alu",
+            "achieved": d["achieved_tflops"], "peak": d["peak_tflops"], "unit": "TFLOP/s", "frac": d["frac"],
+            "traffic": KERNEL_TRAFFIC.get(("k_blend", r.tile)) if args.workload == "hd" else None,
+            "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (no measured FP32 peak)"}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4),

@@ -84,6 +84,7 @@ typedef struct ws_config {
 
 #define WS_CFG_NO_OPACITY_CULL 1u /* ablation: keep splats with sigma < 1/255 */
 #define WS_CFG_NO_AABB_CULL 2u    /* ablation: keep splats whose box misses the viewport */
+#define WS_CFG_SORT_LOOKBACK 4u   /* ws_sort: single-sweep decoupled look-back variant */
 
 /* Library ABI version (WS_ABI_VERSION of the build). */
 int32_t ws_abi_version(void);
@@ -163,6 +164,28 @@ ws_status ws_sort(const uint32_t *num_keys, int64_t key_capacity, int32_t begin_
                   int32_t end_bit, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
                   uint32_t *vals_alt, const ws_config *cfg, void *workspace,
                   int32_t *result_in_alt, void *stream);
+
+/* With cfg->flags & WS_CFG_SORT_LOOKBACK (digit_bits 4..9), ws_sort runs a
+ * single-sweep variant of the same sort: one read of the keys counts the
+ * digits of every pass, then each pass is one kernel over a co-resident
+ * persistent grid in which every block publishes its per-digit counts and
+ * obtains prefix_wg by looking back over its predecessors (decoupled
+ * look-back; release/acquire stores and loads, no read-modify-write
+ * atomics). Its result is bit-identical to the default; only progress
+ * depends on scheduling, and every wait is bounded (about a second): a wait
+ * that runs out raises WS_FLAG_TIMEOUT in the workspace status word, the
+ * other blocks stop, nothing is written out of bounds and the call returns
+ * (the sorted output is then invalid). The paper avoids such inter-block
+ * waiting (§3.3.1); this variant is offered for comparison. */
+
+/* Test hook of the look-back variant: tile `stalled_tile` of the first pass
+ * never publishes its counts, so every later tile's bounded wait runs out.
+ * Lets a test check that a stalled predecessor ends in WS_FLAG_TIMEOUT and a
+ * usable context instead of a hang. Not for production use. */
+ws_status ws_sort_test_stalled_tile(const uint32_t *num_keys, int64_t key_capacity, int32_t begin_bit,
+                                    int32_t end_bit, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                                    uint32_t *vals_alt, const ws_config *cfg, void *workspace,
+                                    int32_t stalled_tile, int32_t *result_in_alt, void *stream);
 
 /* ws_sort without a workspace, for callers that cannot allocate device
  * memory: code running inside an engine that owns every device allocation

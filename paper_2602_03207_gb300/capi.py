@@ -22,13 +22,13 @@ _lib = None
 
 WS_OK, WS_ERR_INVALID_ARG, WS_ERR_CUDA, WS_ERR_CAPACITY, WS_ERR_TIMEOUT, WS_ERR_UNSUPPORTED = range(6)
 WS_FLAG_CAPACITY, WS_FLAG_TIMEOUT = 1, 2
-WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL = 1, 2
+WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL, WS_CFG_SORT_LOOKBACK = 1, 2, 4
 
 EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_preprocess", "ws_cull",
            "ws_sort", "ws_sort_noalloc", "ws_sort_noalloc_max_keys", "ws_rasterize",
            "ws_rasterize_backward", "ws_read_status", "ws_batch_max_views", "ws_batch_workspace_bytes",
            "ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
-           "ws_image_residual")
+           "ws_image_residual", "ws_sort_test_stalled_tile")
 
 
 class WsError(RuntimeError):
@@ -89,6 +89,8 @@ def lib():
             L.ws_rasterize.argtypes = [P, P, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
             L.ws_rasterize_backward.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P, P, P,
                                                 P, P, P, I64, P, P, P, P, P, P, P]
+            L.ws_sort_test_stalled_tile.argtypes = [P, I64, I32, I32, P, P, P, P, cfg_p, P, I32, C.POINTER(I32), P]
+            L.ws_sort_test_stalled_tile.restype = I32
             L.ws_sort_noalloc.argtypes = [P, I64, I32, I32, P, P, P, P, I32, C.POINTER(I32), P]
             L.ws_sort_noalloc.restype = I32
             L.ws_sort_noalloc_max_keys.restype = I64
@@ -103,7 +105,7 @@ def lib():
                                                       P, P, P, P, I64, P, P, P, P, P, P, P]
             L.ws_image_residual.argtypes = [I64, P, P, P, P]
             for name in ("ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
-                         "ws_image_residual"):
+                         "ws_image_residual", "ws_sort_test_stalled_tile"):
                 getattr(L, name).restype = I32
             for name in ("ws_preprocess", "ws_cull", "ws_sort", "ws_rasterize", "ws_rasterize_backward",
                          "ws_read_status"):
@@ -160,6 +162,15 @@ def ws_sort(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, va
         _ptr(num_keys), int(key_capacity), int(begin_bit), int(end_bit), _ptr(keys), _ptr(vals),
         _ptr(keys_alt), _ptr(vals_alt), C.byref(cfg), _ptr(workspace), C.byref(in_alt),
         _stream(stream)))
+    return bool(in_alt.value)
+
+
+def ws_sort_test_stalled_tile(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt, cfg,
+                              workspace, stalled_tile, stream=None) -> bool:
+    in_alt = C.c_int32(0)
+    _check("ws_sort_test_stalled_tile", lib().ws_sort_test_stalled_tile(
+        _ptr(num_keys), int(key_capacity), int(begin_bit), int(end_bit), _ptr(keys), _ptr(vals), _ptr(keys_alt),
+        _ptr(vals_alt), C.byref(cfg), _ptr(workspace), int(stalled_tile), C.byref(in_alt), _stream(stream)))
     return bool(in_alt.value)
 
 

@@ -71,7 +71,10 @@ Layout layout(int64_t n, int64_t cap) {
     Layout L;
     L.status = 0;
     L.sort = align_up(ws::kStatusBytes);
-    L.bwd = L.sort + align_up(ws::sort_scratch_bytes(cap, kMaxDigitBits));
+    const size_t sort_bytes = ws::sort_scratch_bytes(cap, kMaxDigitBits) > ws::sort_lookback_scratch_bytes(cap)
+                                  ? ws::sort_scratch_bytes(cap, kMaxDigitBits)
+                                  : ws::sort_lookback_scratch_bytes(cap);
+    L.bwd = L.sort + align_up(sort_bytes);
     L.cull = L.bwd + align_up(ws::backward_scratch_bytes(cap));
     L.total = L.cull + align_up(ws::cull_scratch_bytes(n));
     return L;
@@ -191,9 +194,39 @@ ws_status ws_sort(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_
     }
     char* ws_base = static_cast<char*>(workspace);
     int in_alt = 0;
-    cudaError_t e = ws::launch_sort(num_keys, key_capacity, begin_bit, end_bit, cfg->digit_bits, keys,
-                                    vals, keys_alt, vals_alt, ws_base + layout(0, key_capacity).sort,
-                                    &in_alt, static_cast<cudaStream_t>(stream));
+    cudaError_t e;
+    if (cfg->flags & WS_CFG_SORT_LOOKBACK) {
+        if (!ws::sort_lookback_supported(cfg->digit_bits, begin_bit, end_bit)) return WS_ERR_UNSUPPORTED;
+        e = ws::launch_sort_lookback(num_keys, key_capacity, begin_bit, end_bit, cfg->digit_bits, keys, vals,
+                                     keys_alt, vals_alt, ws_base + layout(0, key_capacity).sort,
+                                     reinterpret_cast<uint32_t*>(ws_base), -1, &in_alt,
+                                     static_cast<cudaStream_t>(stream));
+    } else {
+        e = ws::launch_sort(num_keys, key_capacity, begin_bit, end_bit, cfg->digit_bits, keys, vals, keys_alt,
+                            vals_alt, ws_base + layout(0, key_capacity).sort, &in_alt,
+                            static_cast<cudaStream_t>(stream));
+    }
+    *result_in_alt = in_alt;
+    return cuda_status(e);
+}
+
+ws_status ws_sort_test_stalled_tile(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_bit,
+                                    int32_t end_bit, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                                    uint32_t* vals_alt, const ws_config* cfg, void* workspace, int32_t stalled_tile,
+                                    int32_t* result_in_alt, void* stream) {
+    if (!cfg || !ws::sort_lookback_supported(cfg->digit_bits, begin_bit, end_bit)) return WS_ERR_UNSUPPORTED;
+    if (key_capacity <= 0 || key_capacity >= (int64_t(1) << 31) || begin_bit < 0 || end_bit > 64 ||
+        begin_bit >= end_bit || !result_in_alt || stalled_tile < 0)
+        return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, workspace, keys, vals, keys_alt, vals_alt};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    char* ws_base = static_cast<char*>(workspace);
+    int in_alt = 0;
+    cudaError_t e = ws::launch_sort_lookback(num_keys, key_capacity, begin_bit, end_bit, cfg->digit_bits, keys, vals,
+                                             keys_alt, vals_alt, ws_base + layout(0, key_capacity).sort,
+                                             reinterpret_cast<uint32_t*>(ws_base), stalled_tile, &in_alt,
+                                             static_cast<cudaStream_t>(stream));
     *result_in_alt = in_alt;
     return cuda_status(e);
 }

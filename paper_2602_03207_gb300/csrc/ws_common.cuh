@@ -218,6 +218,29 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Lanes of the warp holding the same BITS-bit digit as this lane: one ballot
+// per bit (inverted where this lane's bit is 0), ANDed together. Its cost does
+// not depend on how many distinct digits the warp holds. Lanes passing
+// `valid` = false take part in the votes but match no valid lane.
+template <int BITS>
+__device__ __forceinline__ uint32_t warp_match_digit(uint32_t digit, bool valid) {
+    uint32_t peers = __ballot_sync(kFull, valid);
+    if (!valid) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (digit >> b) & 1u;
+        const uint32_t vote = __ballot_sync(kFull, bit);
+        peers &= bit ? vote : ~vote;
+    }
+    return peers;
+}
+
 __device__ __forceinline__ void set_flag(uint32_t* status, uint32_t bit) {
     // A plain store of a fixed value: every writer stores the same bit to
     // its own word, so no read-modify-write is needed.

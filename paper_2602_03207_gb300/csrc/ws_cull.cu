@@ -25,6 +25,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kChunk = kScanThreads * kScanItems;  // Gaussians per block
 constexpr int kTopThreads = 1024;
+constexpr int kSlotCap = 4096;  // slots per chunk resolved through shared memory
 
 // Level 0 up: one sum of tiles_touched per chunk.
 __global__ void __launch_bounds__(kScanThreads)
@@ -85,6 +86,7 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
     __shared__ uint2 s_rect[kChunk];
     __shared__ uint32_t s_depth[kChunk];
     __shared__ uint32_t s_red[kScanThreads / 32 + 1];
+    __shared__ uint16_t s_owner[kSlotCap];  // slot -> local Gaussian (fast path; < kChunk)
     pdl_wait();
     pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * kChunk;
@@ -118,14 +120,66 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
     }
     __syncthreads();
 
-    // Walk the chunk's slot range; slot -> Gaussian by binary search.
+    // Slot -> owning Gaussian. When the chunk's slots fit in shared memory,
+    // every Gaussian with tiles writes its index at its first slot and a
+    // block-wide running maximum fills the rest (indices increase with
+    // slots); otherwise each slot binary-searches the local offsets.
+    const bool fast = total <= (uint32_t)kSlotCap;
+    if (fast) {
+        for (uint32_t e = threadIdx.x; e < total; e += kScanThreads) s_owner[e] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int li = threadIdx.x * kScanItems + k;
+            if (li < cnt && v[k] > 0) s_owner[s_off[li]] = (uint16_t)li;
+        }
+        __syncthreads();
+        // running maximum over the slots: thread-serial over kSlotPer slots, then a block scan
+        constexpr int kSlotPer = kSlotCap / kScanThreads;
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < kSlotPer; ++k) {
+            const int e = threadIdx.x * kSlotPer + k;
+            if (e < (int)total) m = max(m, (uint32_t)s_owner[e]);
+        }
+        // exclusive block max-scan of the per-thread maxima
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t x = m;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x = max(x, y);
+        }
+        __shared__ uint32_t s_wmax[kScanThreads / 32];
+        if (lane == 31) s_wmax[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before = max(before, s_wmax[w]);
+        uint32_t prev = __shfl_up_sync(kFull, x, 1);
+        prev = lane == 0 ? before : max(before, prev);
+#pragma unroll
+        for (int k = 0; k < kSlotPer; ++k) {
+            const int e = threadIdx.x * kSlotPer + k;
+            if (e < (int)total) {
+                prev = max(prev, (uint32_t)s_owner[e]);
+                s_owner[e] = (uint16_t)prev;
+            }
+        }
+        __syncthreads();
+    }
     for (uint32_t s = threadIdx.x; s < total; s += kScanThreads) {
         int64_t slot = (int64_t)coff + s;
         if (slot >= capacity) break;
-        int lo = 0, hi = cnt - 1;  // largest g with s_off[g] <= s
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= s) lo = mid; else hi = mid - 1;
+        int lo;
+        if (fast) {
+            lo = (int)s_owner[s];
+        } else {
+            lo = 0;
+            int hi = cnt - 1;  // largest g with s_off[g] <= s
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= s) lo = mid; else hi = mid - 1;
+            }
         }
         uint32_t j = s - s_off[lo];
         uint2 r = s_rect[lo];

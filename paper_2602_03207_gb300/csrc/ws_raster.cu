@@ -36,8 +36,12 @@ k_zero_ranges(uint2* __restrict__ ranges, uint32_t ntiles) {
 }
 
 // ranges[t] = [start, end) of tile t in the sorted key list. Tiles with no
-// pairs keep the zero range written by k_zero_ranges. Grid-stride over the
-// device-side key count.
+// pairs keep the zero range written by k_zero_ranges. Each warp takes
+// kRangeUnroll consecutive chunks of 32 keys per step, all loads issued
+// before any is used; the next key comes from the neighbour lane (the
+// warp's last lane loads the one past the chunk).
+constexpr int kRangeUnroll = 8;
+
 __global__ void __launch_bounds__(kRangeThreads)
 k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys,
               uint2* __restrict__ ranges, uint32_t ntiles) {
@@ -45,19 +49,27 @@ k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ nu
     pdl_trigger();
     const uint32_t n = *num_keys;
     const int lane = threadIdx.x & 31;
-    // Whole warps step together so the next key comes from the neighbour
-    // lane; the warp's last lane loads the one past the warp.
-    const uint32_t stride = gridDim.x * kRangeThreads;
-    for (uint32_t base = blockIdx.x * kRangeThreads + (threadIdx.x & ~31u); base < n; base += stride) {
-        const uint32_t p = base + lane;
-        const uint32_t t = p < n ? (uint32_t)(__ldg(keys + p) >> 31) : 0xffffffffu;
-        uint32_t next = __shfl_down_sync(kFull, t, 1);
-        if (lane == 31) next = p + 1 < n ? (uint32_t)(__ldg(keys + p + 1) >> 31) : 0xffffffffu;
-        if (p >= n || t >= ntiles) continue;  // past the count / not a key of this grid
-        if (p == 0) ranges[t].x = 0;
-        if (t != next) {
-            ranges[t].y = p + 1;
-            if (p + 1 < n && next < ntiles) ranges[next].x = p + 1;
+    const uint32_t warps = gridDim.x * (kRangeThreads / 32);
+    const uint32_t gw = blockIdx.x * (kRangeThreads / 32) + (threadIdx.x >> 5);
+    for (uint32_t base = gw * 32 * kRangeUnroll; base < n; base += warps * 32 * kRangeUnroll) {
+        uint32_t t[kRangeUnroll], tn[kRangeUnroll];
+#pragma unroll
+        for (int u = 0; u < kRangeUnroll; ++u) {
+            const uint32_t p = base + u * 32 + lane;
+            t[u] = p < n ? (uint32_t)(__ldg(keys + p) >> 31) : 0xffffffffu;
+            tn[u] = (lane == 31 && p + 1 < n) ? (uint32_t)(__ldg(keys + p + 1) >> 31) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < kRangeUnroll; ++u) {
+            const uint32_t p = base + u * 32 + lane;
+            uint32_t next = __shfl_down_sync(kFull, t[u], 1);
+            if (lane == 31) next = tn[u];
+            if (p >= n || t[u] >= ntiles) continue;  // past the count / not a key of this grid
+            if (p == 0) ranges[t[u]].x = 0;
+            if (t[u] != next) {
+                ranges[t[u]].y = p + 1;
+                if (p + 1 < n && next < ntiles) ranges[next].x = p + 1;
+            }
         }
     }
 }

@@ -194,3 +194,14 @@ def test_hd_workload_sampled():
     st = compare_image(g, ref, tile_mask=mask)
     assert st["n_bad"] == 0, st
     assert st["n_multi"] <= 0.001 * st["n_pix"]
+
+
+def test_lookback_sort_frame_identical():
+    """A whole frame with the single-sweep look-back sort is bit-identical
+    to the default wait-free sort."""
+    from paper_2602_03207_gb300 import capi
+    scene, cam = S.small_forward()
+    a = fetch(gpu_frame(scene, cam, digit_bits=8))
+    b = fetch(gpu_frame(scene, cam, digit_bits=8, flags=capi.WS_CFG_SORT_LOOKBACK))
+    for k in ("image", "t_final", "n_contrib", "sorted_keys", "sorted_vals"):
+        np.testing.assert_array_equal(a[k], b[k])

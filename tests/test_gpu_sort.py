@@ -87,3 +87,78 @@ def test_standalone_4m_tile_depth_keys():
     ek, ev = oracle.sort_pairs(keys, vals)
     np.testing.assert_array_equal(k, ek)
     np.testing.assert_array_equal(v, ev)
+
+
+# ---------------------------------------------- single-sweep look-back variant
+
+def gpu_sort_lookback(keys, vals, digit_bits=8, begin_bit=0, end_bit=64):
+    import torch
+    from paper_2602_03207_gb300 import capi
+    n = keys.size
+    cap = max(n, 1)
+    kt = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    vt = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    if n:
+        kt[:n] = torch.from_numpy(keys.view(np.int64))
+        vt[:n] = torch.from_numpy(vals.view(np.int32))
+    ka, va = torch.empty_like(kt), torch.empty_like(vt)
+    num = torch.tensor([n, 0, 0, 0], dtype=torch.int32, device="cuda")
+    cfg = capi.config(digit_bits=digit_bits, flags=capi.WS_CFG_SORT_LOOKBACK)
+    ws = torch.zeros(capi.ws_workspace_bytes(0, cap, capi.camera(S.small_forward()[1]), cfg),
+                     dtype=torch.uint8, device="cuda")
+    in_alt = capi.ws_sort(num, cap, begin_bit, end_bit, kt, vt, ka, va, cfg, ws)
+    assert capi.ws_read_status(ws) == 0
+    k, v = (ka, va) if in_alt else (kt, vt)
+    return k[:n].cpu().numpy().view(np.uint64), v[:n].cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 4097, 24_593, 1_000_000])
+@pytest.mark.parametrize("kind", ["random", "equal", "sorted", "few"])
+def test_lookback_matches_stable_sort(n, kind):
+    rng = np.random.default_rng(n * 3 + len(kind))
+    keys = _keys(kind, n, rng)
+    vals = rng.permutation(n).astype(np.uint32)
+    k, v = gpu_sort_lookback(keys, vals, digit_bits=8, end_bit=45)
+    ek, ev = oracle.sort_pairs(keys, vals)
+    np.testing.assert_array_equal(k, ek)
+    np.testing.assert_array_equal(v, ev)
+
+
+@pytest.mark.parametrize("bits", [4, 5, 6, 7, 8, 9])
+def test_lookback_digit_widths(bits):
+    rng = np.random.default_rng(100 + bits)
+    keys = rng.integers(0, 2 ** 50, 200_000, dtype=np.uint64)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    k, v = gpu_sort_lookback(keys, vals, digit_bits=bits, begin_bit=3, end_bit=50)
+    perm = np.argsort(keys >> np.uint64(3), kind="stable")
+    np.testing.assert_array_equal(k, keys[perm])
+    np.testing.assert_array_equal(v, vals[perm])
+
+
+def test_lookback_stalled_tile_times_out_instead_of_hanging():
+    """A predecessor that never publishes makes every later tile's bounded
+    wait run out: the call returns, WS_FLAG_TIMEOUT is raised, and the
+    context stays usable (a normal sort right after is correct)."""
+    import time
+    import torch
+    from paper_2602_03207_gb300 import capi
+    rng = np.random.default_rng(7)
+    n = 50_000  # 25 tiles of 2048 keys
+    keys = rng.integers(0, 2 ** 40, n, dtype=np.uint64)
+    vals = np.arange(n, dtype=np.uint32)
+    kt = torch.from_numpy(keys.view(np.int64)).cuda()
+    vt = torch.from_numpy(vals.view(np.int32)).cuda()
+    ka, va = torch.empty_like(kt), torch.empty_like(vt)
+    num = torch.tensor([n, 0, 0, 0], dtype=torch.int32, device="cuda")
+    cfg = capi.config(digit_bits=8, flags=capi.WS_CFG_SORT_LOOKBACK)
+    ws = torch.zeros(capi.ws_workspace_bytes(0, n, capi.camera(S.small_forward()[1]), cfg),
+                     dtype=torch.uint8, device="cuda")
+    t0 = time.time()
+    capi.ws_sort_test_stalled_tile(num, n, 0, 40, kt, vt, ka, va, cfg, ws, 3)
+    flags = capi.ws_read_status(ws)
+    assert flags & capi.WS_FLAG_TIMEOUT
+    assert time.time() - t0 < 30
+    k, v = gpu_sort_lookback(keys, vals, digit_bits=8, end_bit=40)
+    ek, ev = oracle.sort_pairs(keys, vals)
+    np.testing.assert_array_equal(k, ek)
+    np.testing.assert_array_equal(v, ev)
