@@ -32,6 +32,7 @@ WORKLOADS = {
     "uhd": {"desc": "6,000,000 Gaussians, 3840x2160, SH3, 8 orbit poses", "n": 6_000_000},
 }
 METRIC = "1080p frames/s at 1M splats"
+METRICS = {"hd": METRIC, "uhd": "2160p frames/s at 6M splats"}
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel on the hd workload (profiles/kernels_hd_1080p_1M.md); to be reset
 # to None whenever that kernel changes.
@@ -215,6 +216,64 @@ def sort_only(dev, steps=50, digit_bits=9):
             "gkeys_s": round(n / med / 1e9, 3), "achieved_gbs": round(gbs, 1)}
 
 
+def ablation_table(scene, cams, tile, digit_bits, dev, frames=40):
+    """§4.4 / Table 5 style: per-stage times (CUDA events), pairs and peak
+    device memory for the full pipeline and each ablation (-CULL: no viewport
+    AABB culling; -RADIUS: opacity-independent box; -OPACITY: no sigma < 1/255
+    culling). Every variant renders the same image; only the work differs."""
+    import torch
+    from paper_2602_03207_gb300 import capi, render
+    n = scene["means"].shape[0]
+    W, H = cams[0]["width"], cams[0]["height"]
+    variants = {"full": 0, "-cull": capi.WS_CFG_NO_AABB_CULL, "-radius": capi.WS_CFG_FIXED_RADIUS,
+                "-opacity": capi.WS_CFG_NO_OPACITY_CULL}
+    out = {}
+    for name, flags in variants.items():
+        # the cull's scan counts every pair even past the capacity
+        probe = render.Renderer(n, W, H, tile=tile, digit_bits=digit_bits, key_capacity=4096, flags=flags,
+                                device=dev)
+        kmax = 0
+        for cam in cams:
+            probe.forward(scene, cam)
+            kmax = max(kmax, probe.total_pairs())
+        del probe
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats(dev)
+        base_mem = torch.cuda.memory_allocated(dev)
+        cap = int(math.ceil(kmax * 1.15 / 4096) * 4096)
+        r = render.Renderer(n, W, H, tile=tile, digit_bits=digit_bits, key_capacity=cap, flags=flags, device=dev)
+        for i in range(3):
+            r.forward(scene, cams[i % len(cams)])
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(frames)]
+        pairs = 0
+        for i in range(frames):
+            cam = capi.camera(cams[i % len(cams)])
+            e = ev[i]
+            e[0].record()
+            r.preprocess(scene, cam)
+            e[1].record()
+            r.cull(cam)
+            e[2].record()
+            r.sort()
+            e[3].record()
+            r.rasterize(cam)
+            e[4].record()
+        torch.cuda.synchronize()
+        r.check_status()
+        st = {s: sum(e[j].elapsed_time(e[j + 1]) for e in ev) / frames for j, s in enumerate(STAGES)}
+        for cam in cams:
+            r.forward(scene, cam)
+            torch.cuda.synchronize()
+            pairs += r.key_count()
+        out[name] = {"stages_ms": {k: round(v, 4) for k, v in st.items()}, "total_ms": round(sum(st.values()), 4),
+                     "mean_pairs": int(pairs / len(cams)),
+                     "peak_frame_bytes": int(torch.cuda.max_memory_allocated(dev) - base_mem)}
+        del r
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -390,7 +449,7 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
             "traffic": KERNEL_TRAFFIC.get(("k_blend", r.tile)) if args.workload == "hd" else None,
             "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (no measured FP32 peak)"}
     out = {
-        "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
+        "metric": METRICS.get(args.workload, METRIC), "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded 64-cluster scene standing in for the paper's trained captures)",
@@ -406,6 +465,9 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
         "clocks": clocks,
     }
     out["sort_only"] = sort_only(r.image.device, digit_bits=args.digit_bits)
+    if not args.no_ablation:
+        out["ablation"] = ablation_table(scene, cams, r.tile, args.digit_bits, r.image.device,
+                                         frames=40 if args.workload == "hd" else 16)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
     return out
@@ -534,7 +596,7 @@ def run_reference(args):
         oracle.render(sub, cams[i % 8])
     dt = time.perf_counter() - t
     value = args.steps / frac / dt
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "frames/s",
+    return {"impl": "reference", "metric": METRICS.get(args.workload, METRIC), "value": round(value, 4), "unit": "frames/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -556,6 +618,7 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=9)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     res = run_reference(args) if args.impl == "reference" else run_ours(args)

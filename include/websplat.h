@@ -85,6 +85,7 @@ typedef struct ws_config {
 #define WS_CFG_NO_OPACITY_CULL 1u /* ablation: keep splats with sigma < 1/255 */
 #define WS_CFG_NO_AABB_CULL 2u    /* ablation: keep splats whose box misses the viewport */
 #define WS_CFG_SORT_LOOKBACK 4u   /* ws_sort: single-sweep decoupled look-back variant */
+#define WS_CFG_FIXED_RADIUS 8u    /* ablation: every splat's box as at sigma = 1 (no opacity-aware extent) */
 
 /* Library ABI version (WS_ABI_VERSION of the build). */
 int32_t ws_abi_version(void);

@@ -23,7 +23,8 @@ _LIB_PATH = os.path.join(_OUT_DIR, "libws_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DEFAULTS = {"tile": 16, "dilation": 0.3, "guard": 1.3, "amb_px_rel": 1e-6, "amb_alpha": 1e-4}
+DEFAULTS = {"tile": 16, "dilation": 0.3, "guard": 1.3, "amb_px_rel": 1e-6, "amb_alpha": 1e-4, "flags": 0}
+NO_OPACITY_CULL, NO_AABB_CULL, FIXED_RADIUS = 1, 2, 8
 REASONS = {0: "visible", 1: "opacity", 2: "quat", 3: "near", 4: "det", 5: "offscreen"}
 
 
@@ -48,7 +49,7 @@ class _Camera(C.Structure):
 
 class _Config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("dilation", C.c_double), ("guard", C.c_double),
-                ("amb_px_rel", C.c_double), ("amb_alpha", C.c_double)]
+                ("amb_px_rel", C.c_double), ("amb_alpha", C.c_double), ("flags", C.c_int32)]
 
 
 _D = C.POINTER(C.c_double)
@@ -113,7 +114,7 @@ def config(**kw):
     d = dict(DEFAULTS)
     d.update({k: v for k, v in kw.items() if v is not None})
     return _Config(int(d["tile"]), float(d["dilation"]), float(d["guard"]),
-                   float(d["amb_px_rel"]), float(d["amb_alpha"]))
+                   float(d["amb_px_rel"]), float(d["amb_alpha"]), int(d["flags"]))
 
 
 def tiles(cam, tile=16):

@@ -84,7 +84,10 @@ typedef struct {
     double guard;        /* frustum guard factor of the Jacobian clamp */
     double amb_px_rel;   /* relative margin of tile-bound / viewport decisions */
     double amb_alpha;    /* relative margin of the per-pixel 1/255 decision */
+    int32_t flags;       /* ablations (§4.4): 1 keep sigma < 1/255, 2 keep off-screen boxes, 8 fixed extent */
 } or_config;
+
+enum { OR_NO_OPACITY_CULL = 1, OR_NO_AABB_CULL = 2, OR_FIXED_RADIUS = 8 };
 
 enum { OR_VISIBLE = 0, OR_CULL_OPACITY = 1, OR_CULL_QUAT = 2, OR_CULL_NEAR = 3,
        OR_CULL_DET = 4, OR_CULL_OFFSCREEN = 5 };
@@ -254,7 +257,7 @@ int64_t or_preprocess(int64_t n, const double *means, const double *log_scales,
         double logit = logits[i];
         double sigma = 1.0 / (1.0 + exp(-logit));
         opacity[i] = sigma;
-        if (logit < tau_opacity()) { reason[i] = OR_CULL_OPACITY; continue; }
+        if (logit < tau_opacity() && !(cfg->flags & OR_NO_OPACITY_CULL)) { reason[i] = OR_CULL_OPACITY; continue; }
         const double *q0 = quats + 4 * i;
         double qn = sqrt(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + q0[3] * q0[3]);
         if (qn == 0.0) { reason[i] = OR_CULL_QUAT; continue; }
@@ -322,6 +325,9 @@ int64_t or_preprocess(int64_t n, const double *means, const double *log_scales,
          * half-widths sqrt(q_c Sigma'_xx), sqrt(q_c Sigma'_yy). */
         double qc = 2.0 * log(255.0 * sigma);
         if (qc < 0.0) qc = 0.0;
+        /* ablation "-RADIUS" (§4.4, Table 5): a box independent of the
+         * opacity, the one a splat of sigma = 1 needs */
+        if (cfg->flags & OR_FIXED_RADIUS) qc = 2.0 * log(255.0);
         double ex = sqrt(qc * sxx), ey = sqrt(qc * syy);
         extent[2 * i] = ex; extent[2 * i + 1] = ey;
 
@@ -335,17 +341,20 @@ int64_t or_preprocess(int64_t n, const double *means, const double *log_scales,
             if (!(hi[a] >= -eps && lo[a] < lim[a] + eps)) on_relaxed = 0;
             if (fabs(hi[a]) < eps || fabs(lo[a] - lim[a]) < eps) amb[i] = 1;
         }
-        if (on_relaxed) {
+        if (on_relaxed || (cfg->flags & OR_NO_AABB_CULL)) {
             /* Widened rectangle: every tile either rounding could select. */
-            int x0 = (int)fmax(0.0, flr((lo[0] - eps) / TS)), x1 = (int)fmin(TX - 1.0, flr((hi[0] + eps) / TS));
-            int y0 = (int)fmax(0.0, flr((lo[1] - eps) / TS)), y1 = (int)fmin(TY - 1.0, flr((hi[1] + eps) / TS));
+            int x0 = (int)fmin(TX - 1.0, fmax(0.0, flr((lo[0] - eps) / TS)));
+            int x1 = (int)fmin(TX - 1.0, fmax(0.0, flr((hi[0] + eps) / TS)));
+            int y0 = (int)fmin(TY - 1.0, fmax(0.0, flr((lo[1] - eps) / TS)));
+            int y1 = (int)fmin(TY - 1.0, fmax(0.0, flr((hi[1] + eps) / TS)));
             re[0] = x0; re[1] = y0; re[2] = x1; re[3] = y1;
         }
-        if (!on) { reason[i] = OR_CULL_OFFSCREEN; continue; }
+        /* ablation "-CULL" (§4.4): off-screen boxes are kept, clamped to the screen */
+        if (!on && !(cfg->flags & OR_NO_AABB_CULL)) { reason[i] = OR_CULL_OFFSCREEN; continue; }
         /* Tile rectangle: tiles whose column / row range holds a pixel centre
          * of [m - e, m + e] (tile k covers [k TS, (k+1) TS)). */
-        int x0 = (int)fmax(0.0, flr(lo[0] / TS)), x1 = (int)fmin(TX - 1.0, flr(hi[0] / TS));
-        int y0 = (int)fmax(0.0, flr(lo[1] / TS)), y1 = (int)fmin(TY - 1.0, flr(hi[1] / TS));
+        int x0 = (int)fmin(TX - 1.0, fmax(0.0, flr(lo[0] / TS))), x1 = (int)fmin(TX - 1.0, fmax(0.0, flr(hi[0] / TS)));
+        int y0 = (int)fmin(TY - 1.0, fmax(0.0, flr(lo[1] / TS))), y1 = (int)fmin(TY - 1.0, fmax(0.0, flr(hi[1] / TS)));
         for (int a = 0; a < 2; ++a) {
             double vv[2] = {lo[a], hi[a]};
             int ntile = a == 0 ? TX : TY;

@@ -74,7 +74,7 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
             // small margin so rounding never drops a pair the per-pixel test
             // would keep: half-widths sqrt(q_c Sigma'_xx), sqrt(q_c Sigma'_yy).
             const float det = fmaf(a, c, -b * b);
-            const float qc = fmaxf(0.f, 2.f * (kLn255 + __logf(op)));
+            const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, 2.f * (kLn255 + __logf(op)));
             const float ex = sqrtf(qc * c / det) * 1.0001f + 1e-3f;
             const float ey = sqrtf(qc * a / det) * 1.0001f + 1e-3f;
             // blocks whose pixel centres [8c + .5, 8c + 7.5] x [4r + .5, 4r + 3.5] meet the box
@@ -231,7 +231,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
             r.col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), c);
             s_rec[j] = r;
             const float det = fmaf(a, c, -b * b);
-            const float qc = fmaxf(0.f, 2.f * (kLn255 + __logf(op)));
+            const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, 2.f * (kLn255 + __logf(op)));
             const float ex = sqrtf(qc * c / det) * 1.0001f + 1e-3f;
             const float ey = sqrtf(qc * a / det) * 1.0001f + 1e-3f;
             const float c0 = fmaxf(0.f, ceilf((r.geo.x - ex - (BW - 0.5f)) * (1.f / BW)));

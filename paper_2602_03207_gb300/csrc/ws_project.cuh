@@ -131,7 +131,9 @@ __device__ __forceinline__ bool project_splat(const Frame& f, float x, float y, 
     // sigma and the opacity-aware extent (§3.4): q_c = 2 ln(255 sigma)
     const float en = expf(-logit);
     P.sigma = 1.f / (1.f + en);
-    const float qc = fmaxf(0.f, 2.f * (kLn255 - log1pf(en)));
+    // WS_CFG_FIXED_RADIUS (ablation): the box every splat would need at
+    // sigma = 1, independent of its opacity (conservative, only larger).
+    const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, 2.f * (kLn255 - log1pf(en)));
     const float ex = sqrtf(qc * sxx), ey = sqrtf(qc * syy);
     const float lox = __fadd_rn(__fsub_rn(mx.hi, ex), mx.lo), hix = __fadd_rn(__fadd_rn(mx.hi, ex), mx.lo);
     const float loy = __fadd_rn(__fsub_rn(my.hi, ey), my.lo), hiy = __fadd_rn(__fadd_rn(my.hi, ey), my.lo);

@@ -205,3 +205,25 @@ def test_lookback_sort_frame_identical():
     b = fetch(gpu_frame(scene, cam, digit_bits=8, flags=capi.WS_CFG_SORT_LOOKBACK))
     for k in ("image", "t_final", "n_contrib", "sorted_keys", "sorted_vals"):
         np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("flags", [1, 2, 8, 11])
+def test_ablation_flags(flags):
+    """§4.4 ablations (1: keep sigma < 1/255, 2: -CULL keeps off-screen
+    boxes, 8: -RADIUS opacity-independent box): parity with the oracle under
+    the same flag, and an image bit-identical to the default (they only add
+    pairs whose alpha is below 1/255)."""
+    scene = S.uniform_scene(4000, seed=52)
+    scene["opacity_logits"][:300] = -7.0
+    cam = S.look_at_camera((2.2, -1.0, 0.8), (0.4, 0.0, 0.0), 160, 120)
+    g = fetch(gpu_frame(scene, cam, flags=flags, key_capacity=40 * 4000))
+    ref = oracle.render(scene, cam, flags=flags)
+    _check_preprocess(g, ref)
+    _check_emission(g, ref)
+    _check_sort(g)
+    st = compare_image(g, ref)
+    assert st["n_bad"] == 0, st
+    base = fetch(gpu_frame(scene, cam, key_capacity=40 * 4000))
+    np.testing.assert_array_equal(g["image"], base["image"])
+    np.testing.assert_array_equal(g["t_final"], base["t_final"])
+    assert g["num_keys"] > base["num_keys"]

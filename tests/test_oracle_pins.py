@@ -380,3 +380,20 @@ def test_gradient_matches_central_differences(big):
         # sanity: gradients are non-trivial
         assert np.linalg.norm(g[mask]) > 0, name
     assert skipped < 0.02 * (checked + skipped)
+
+
+def test_ablations_leave_the_image_unchanged():
+    """§4.4's ablations only add work: keeping sigma < 1/255 splats, keeping
+    off-screen boxes (-CULL) and the opacity-independent box (-RADIUS) do not
+    change the image, because every added pair has alpha < 1/255. They do
+    add (tile, splat) pairs."""
+    scene = S.uniform_scene(600, seed=51)
+    scene["opacity_logits"][:60] = -7.0  # below 1/255
+    cam = S.look_at_camera((2.2, -1.0, 0.8), (0.4, 0.0, 0.0), 64, 48)
+    base = oracle.render(scene, cam)
+    for flags in (oracle.NO_OPACITY_CULL, oracle.NO_AABB_CULL, oracle.FIXED_RADIUS,
+                  oracle.NO_OPACITY_CULL | oracle.NO_AABB_CULL | oracle.FIXED_RADIUS):
+        out = oracle.render(scene, cam, flags=flags)
+        ok = (base["n_amb"] == 0) & (out["n_amb"] == 0)
+        np.testing.assert_allclose(out["image"][ok], base["image"][ok], atol=1e-14)
+        assert out["keys"].size > base["keys"].size
