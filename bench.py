@@ -133,6 +133,22 @@ def sort_bytes(keys, passes):
     return 32 * keys * passes
 
 
+def seg_partition_passes(end_bit):
+    """Passes of the segmented sort's partition over bits [31, end_bit)."""
+    return max(1, math.ceil((end_bit - 31) / 8))
+
+
+def seg_sort_bytes(keys, end_bit):
+    """Segmented sort: the partition's LSD passes (32 B per key each), the
+    bounds kernel's read of the keys (8 B) and the local sort's read and
+    write of key and value (24 B)."""
+    return sort_bytes(keys, seg_partition_passes(end_bit)) + 32 * keys
+
+
+def seg_sort_launches(end_bit):
+    return 3 * seg_partition_passes(end_bit) + 2
+
+
 def blend_work(fetched, width, height, tile):
     """Evaluations the blend must make: for every (tile, splat) pair, the
     tile's pixel centres inside the splat's opacity-aware extent box; and the
@@ -185,7 +201,8 @@ def whole_job_rate(units_per_rank, world, seconds):
 def sort_only(dev, steps=50, digit_bits=9):
     """Sort-only throughput: the 4,194,304-key (tile, depth) array, 44 bits,
     timed with CUDA events around each ws_sort call (input copied in
-    between, outside the timed span)."""
+    between, outside the timed span), for the segmented sort (the
+    renderer's) and the full-key LSD passes; both give the same output."""
     import torch
     from paper_2602_03207_gb300 import capi, synthetic as S
     k4, v4 = S.sort_keys()
@@ -194,26 +211,32 @@ def sort_only(dev, steps=50, digit_bits=9):
     vv = torch.from_numpy(v4.view(np.int32)).to(dev)
     k1, v1, k2, v2 = torch.empty_like(kk), torch.empty_like(vv), torch.empty_like(kk), torch.empty_like(vv)
     num = torch.tensor([n, 0, 0, 0], dtype=torch.int32, device=dev)
-    cfg = capi.config(digit_bits=digit_bits)
     cam = capi.camera(S.small_forward()[1])
-    ws = torch.zeros(capi.ws_workspace_bytes(0, n, cam, cfg), dtype=torch.uint8, device=dev)
-    ts = []
-    for it in range(steps + 5):
-        k1.copy_(kk)
-        v1.copy_(vv)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        capi.ws_sort(num, n, 0, 44, k1, v1, k2, v2, cfg, ws)
-        b.record()
-        torch.cuda.synchronize()
-        if it >= 5:
-            ts.append(a.elapsed_time(b))
-    ts.sort()
-    med = ts[len(ts) // 2] * 1e-3
-    passes = math.ceil(44 / digit_bits)
-    gbs = sort_bytes(n, passes) / med / 1e9
-    return {"keys": n, "key_bits": 44, "digit_bits": digit_bits, "median_ms": round(med * 1e3, 4),
-            "gkeys_s": round(n / med / 1e9, 3), "achieved_gbs": round(gbs, 1)}
+    out = {}
+    for variant, flags in (("segmented", capi.WS_CFG_SORT_SEGMENTED), ("lsd", 0)):
+        cfg = capi.config(digit_bits=digit_bits, flags=flags)
+        ws = torch.zeros(capi.ws_workspace_bytes(0, n, cam, cfg), dtype=torch.uint8, device=dev)
+        ts = []
+        for it in range(steps + 5):
+            k1.copy_(kk)
+            v1.copy_(vv)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            capi.ws_sort(num, n, 0, 44, k1, v1, k2, v2, cfg, ws)
+            b.record()
+            torch.cuda.synchronize()
+            if it >= 5:
+                ts.append(a.elapsed_time(b))
+        ts.sort()
+        med = ts[len(ts) // 2] * 1e-3
+        alg = seg_sort_bytes(n, 44) if flags else sort_bytes(n, math.ceil(44 / digit_bits))
+        out[variant] = {"median_ms": round(med * 1e3, 4), "gkeys_s": round(n / med / 1e9, 3),
+                        "achieved_gbs": round(alg / med / 1e9, 1)}
+        del ws
+    best = out["segmented"]
+    return {"keys": n, "key_bits": 44, "variant": "segmented", "digit_bits": digit_bits,
+            "median_ms": best["median_ms"], "gkeys_s": best["gkeys_s"], "achieved_gbs": best["achieved_gbs"],
+            "lsd": out["lsd"]}
 
 
 def ablation_table(scene, cams, tile, digit_bits, dev, frames=40):
@@ -308,7 +331,9 @@ def run_ours(args):
     r = render.Renderer(n, W, H, tile=args.tile, digit_bits=args.digit_bits, key_capacity=cap, device=dev)
     stream = torch.cuda.current_stream(dev)
     passes = math.ceil(r.end_bit / args.digit_bits)
-    launches_per_frame = 1 + 3 + 3 * passes + 3  # preprocess, cull (3), sort (3 per pass), raster (3)
+    # preprocess, cull (3), sort (segmented: 3 per partition pass + bounds +
+    # local), raster (3)
+    launches_per_frame = 1 + 3 + seg_sort_launches(r.end_bit) + 3
 
     # warm-up
     for i in range(args.warmup):
@@ -417,7 +442,7 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
     vis, opok, keys = tot["vis"] / 8, tot["opok"] / 8, tot["keys"] / 8
     b_pre = preprocess_bytes(n, opok, vis)
     b_cull = cull_bytes(n, keys)
-    b_sort = sort_bytes(keys, passes)
+    b_sort = seg_sort_bytes(keys, r.end_bit)
     stages = {}
     for s, b in (("preprocess", b_pre), ("cull", b_cull), ("sort", b_sort)):
         ms = stage_ms[s]

@@ -86,6 +86,7 @@ typedef struct ws_config {
 #define WS_CFG_NO_AABB_CULL 2u    /* ablation: keep splats whose box misses the viewport */
 #define WS_CFG_SORT_LOOKBACK 4u   /* ws_sort: single-sweep decoupled look-back variant */
 #define WS_CFG_FIXED_RADIUS 8u    /* ablation: every splat's box as at sigma = 1 (no opacity-aware extent) */
+#define WS_CFG_SORT_SEGMENTED 16u /* ws_sort: partition by bits [31, end) then sort each segment on chip */
 
 /* Library ABI version (WS_ABI_VERSION of the build). */
 int32_t ws_abi_version(void);
@@ -178,6 +179,20 @@ ws_status ws_sort(const uint32_t *num_keys, int64_t key_capacity, int32_t begin_
  * other blocks stop, nothing is written out of bounds and the call returns
  * (the sorted output is then invalid). The paper avoids such inter-block
  * waiting (§3.3.1); this variant is offered for comparison. */
+
+/* With cfg->flags & WS_CFG_SORT_SEGMENTED (and not WS_CFG_SORT_LOOKBACK),
+ * ws_sort treats bits [31, end_bit) of each key as a segment id (the tile of
+ * a (tile << 31 | depth) key) and bits [begin_bit, 31) as its sub-key. It
+ * partitions the pairs by segment with the wait-free passes above, finds
+ * every segment's first position, and sorts each segment by its sub-key on
+ * chip (a warp per segment of at most 256 keys, a block otherwise). The
+ * output, ties included, is bit-identical to the default, with fewer passes
+ * over the whole key array (13 tile bits: 2 instead of 5 at 9-bit digits).
+ * It applies when 0 <= begin_bit < 31 < end_bit <= 55 and the workspace's
+ * sort region holds the 2^(end_bit - 31) + 1 segment starts (at about
+ * 1792 segments per 2048 keys of capacity); otherwise ws_sort runs the
+ * default sort. Segments of more than 2048 keys are sorted by one block
+ * through global memory, correct at any size but slower. */
 
 /* Test hook of the look-back variant: tile `stalled_tile` of the first pass
  * never publishes its counts, so every later tile's bounded wait runs out.

@@ -14,18 +14,19 @@ import math
 import torch
 
 from . import capi
-from .render import SCENE_KEYS, tile_grid
+from .render import SCENE_KEYS, config_flags, tile_grid
 
 
 class BatchRenderer:
     def __init__(self, n, cams, tile=16, digit_bits=9, key_capacity=None, dilation=0.3, guard=1.3, flags=0,
-                 device="cuda"):
+                 device="cuda", sort="segmented"):
         if not 0 < len(cams) <= capi.ws_batch_max_views():
             raise ValueError(f"1..{capi.ws_batch_max_views()} views per batch")
         self.n, self.V = int(n), len(cams)
         self.cams = list(cams)
         self.cams_arr = capi.camera_array(cams)
-        self.cfg = capi.config(tile=tile, digit_bits=digit_bits, dilation=dilation, guard=guard, flags=flags)
+        self.cfg = capi.config(tile=tile, digit_bits=digit_bits, dilation=dilation, guard=guard,
+                               flags=config_flags(flags, sort))
         self.tile = tile
         grids = [tile_grid(c["width"], c["height"], tile) for c in cams]
         self.tile_off = [0]

@@ -23,6 +23,7 @@ _lib = None
 WS_OK, WS_ERR_INVALID_ARG, WS_ERR_CUDA, WS_ERR_CAPACITY, WS_ERR_TIMEOUT, WS_ERR_UNSUPPORTED = range(6)
 WS_FLAG_CAPACITY, WS_FLAG_TIMEOUT = 1, 2
 WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL, WS_CFG_SORT_LOOKBACK, WS_CFG_FIXED_RADIUS = 1, 2, 4, 8
+WS_CFG_SORT_SEGMENTED = 16
 
 EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_preprocess", "ws_cull",
            "ws_sort", "ws_sort_noalloc", "ws_sort_noalloc_max_keys", "ws_rasterize",

@@ -201,6 +201,11 @@ ws_status ws_sort(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_
                                      keys_alt, vals_alt, ws_base + layout(0, key_capacity).sort,
                                      reinterpret_cast<uint32_t*>(ws_base), -1, &in_alt,
                                      static_cast<cudaStream_t>(stream));
+    } else if ((cfg->flags & WS_CFG_SORT_SEGMENTED) &&
+               ws::sort_segmented_supported(key_capacity, begin_bit, end_bit)) {
+        e = ws::launch_sort_segmented(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt,
+                                      ws_base + layout(0, key_capacity).sort, &in_alt,
+                                      static_cast<cudaStream_t>(stream));
     } else {
         e = ws::launch_sort(num_keys, key_capacity, begin_bit, end_bit, cfg->digit_bits, keys, vals, keys_alt,
                             vals_alt, ws_base + layout(0, key_capacity).sort, &in_alt,

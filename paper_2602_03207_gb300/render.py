@@ -35,14 +35,27 @@ def key_end_bit(width, height, tile):
     return 31 + max(1, math.ceil(math.log2(tiles))) if tiles > 1 else 31
 
 
+SORT_FLAGS = {"segmented": capi.WS_CFG_SORT_SEGMENTED, "lsd": 0, "lookback": capi.WS_CFG_SORT_LOOKBACK}
+
+
+def config_flags(flags, sort):
+    """ws_config.flags for the user's flags and a sort variant: "segmented"
+    (partition by tile, then each tile's depths on chip), "lsd" (full-key
+    passes) or "lookback" (single-sweep look-back passes). All three give
+    the same sorted pairs."""
+    if sort not in SORT_FLAGS:
+        raise ValueError(f"sort must be one of {sorted(SORT_FLAGS)}, got {sort!r}")
+    return int(flags) | SORT_FLAGS[sort]
+
+
 class Renderer:
     """Buffers and calls for frames of a fixed (n, width, height, tile)."""
 
     def __init__(self, n, width, height, tile=16, digit_bits=8, key_capacity=None, dilation=0.3,
-                 guard=1.3, flags=0, device="cuda"):
+                 guard=1.3, flags=0, device="cuda", sort="segmented"):
         self.n, self.width, self.height = int(n), int(width), int(height)
         self.cfg = capi.config(tile=tile, digit_bits=digit_bits, dilation=dilation, guard=guard,
-                               flags=flags)
+                               flags=config_flags(flags, sort))
         self.tile = tile
         self.tx, self.ty = tile_grid(width, height, tile)
         self.key_capacity = int(key_capacity if key_capacity is not None else max(1024, 4 * self.n))
@@ -153,13 +166,13 @@ class Renderer:
         return int(self.offsets[self.n].item()) & 0xFFFFFFFF
 
 
-def render(scene, cam_dict, tile=16, digit_bits=8, key_capacity=None, flags=0):
+def render(scene, cam_dict, tile=16, digit_bits=8, key_capacity=None, flags=0, sort="segmented"):
     """Render one frame of a device scene dict; returns (image, renderer).
 
     Raises when the pair list overflows the key capacity (after a sync)."""
     n = scene["means"].shape[0]
     r = Renderer(n, cam_dict["width"], cam_dict["height"], tile=tile, digit_bits=digit_bits,
-                 key_capacity=key_capacity, flags=flags, device=scene["means"].device)
+                 key_capacity=key_capacity, flags=flags, device=scene["means"].device, sort=sort)
     img = r.forward(scene, cam_dict)
     r.check_status()
     return img, r

@@ -227,3 +227,23 @@ def test_ablation_flags(flags):
     np.testing.assert_array_equal(g["image"], base["image"])
     np.testing.assert_array_equal(g["t_final"], base["t_final"])
     assert g["num_keys"] > base["num_keys"]
+
+
+def test_sort_variants_give_identical_frames():
+    """The segmented sort (the renderer's default), the full-key passes and
+    the look-back passes sort the 1M-splat 1080p pair list identically."""
+    import torch
+    from paper_2602_03207_gb300 import capi, render
+    scene = render.scene_to_device(S.hd_scene())
+    cam = S.hd_camera(1)
+    out = {}
+    for sort in ("segmented", "lsd", "lookback"):
+        r = render.Renderer(1_000_000, 1920, 1080, digit_bits=8, key_capacity=1_400_000, sort=sort)
+        r.forward(scene, cam)
+        r.check_status()
+        torch.cuda.synchronize()
+        k = r.key_count()
+        out[sort] = (r.sorted_keys[:k].cpu().numpy(), r.sorted_vals[:k].cpu().numpy(), r.image.cpu().numpy())
+    for sort in ("lsd", "lookback"):
+        for a, b in zip(out["segmented"], out[sort]):
+            np.testing.assert_array_equal(a, b)

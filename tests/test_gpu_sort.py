@@ -10,7 +10,7 @@ from paper_2602_03207_gb300 import synthetic as S
 pytestmark = pytest.mark.gpu
 
 
-def gpu_sort(keys, vals, digit_bits=8, begin_bit=0, end_bit=64, capacity=None):
+def gpu_sort(keys, vals, digit_bits=8, begin_bit=0, end_bit=64, capacity=None, flags=0):
     import torch
     from paper_2602_03207_gb300 import capi
     n = keys.size
@@ -23,7 +23,7 @@ def gpu_sort(keys, vals, digit_bits=8, begin_bit=0, end_bit=64, capacity=None):
     ka = torch.empty_like(kt)
     va = torch.empty_like(vt)
     num = torch.tensor([n, 0, 0, 0], dtype=torch.int32, device="cuda")
-    cfg = capi.config(digit_bits=digit_bits)
+    cfg = capi.config(digit_bits=digit_bits, flags=flags)
     cam = capi.camera(S.small_forward()[1])
     ws = torch.zeros(capi.ws_workspace_bytes(0, cap, cam, cfg), dtype=torch.uint8, device="cuda")
     in_alt = capi.ws_sort(num, cap, begin_bit, end_bit, kt, vt, ka, va, cfg, ws)
@@ -159,6 +159,81 @@ def test_lookback_stalled_tile_times_out_instead_of_hanging():
     assert flags & capi.WS_FLAG_TIMEOUT
     assert time.time() - t0 < 30
     k, v = gpu_sort_lookback(keys, vals, digit_bits=8, end_bit=40)
+    ek, ev = oracle.sort_pairs(keys, vals)
+    np.testing.assert_array_equal(k, ek)
+    np.testing.assert_array_equal(v, ev)
+
+
+# ---------------------------------------------------------------- segmented
+SEG = 16  # WS_CFG_SORT_SEGMENTED
+
+
+def _tile_depth_keys(sizes, rng, depth_levels=None):
+    """(tile << 31) | float32 depth bits, tile t holding sizes[t] keys, in a
+    shuffled (emission-like) order; depth_levels forces ties."""
+    tiles = np.repeat(np.arange(len(sizes), dtype=np.uint64), sizes)
+    if depth_levels:
+        depth = rng.integers(1, depth_levels + 1, tiles.size).astype(np.float32)
+    else:
+        depth = rng.uniform(0.2, 80.0, tiles.size).astype(np.float32)
+    keys = (tiles << np.uint64(31)) | depth.view(np.uint32).astype(np.uint64)
+    perm = rng.permutation(keys.size)
+    return keys[perm], perm.astype(np.uint32)
+
+
+@pytest.mark.parametrize("ties", [None, 3])
+def test_segmented_sort_all_segment_paths(ties):
+    """Segment sizes around every path boundary of the segmented sort: one
+    warp (<= 256 keys), the block in shared memory (<= 2048) and the block
+    through global memory (> 2048), plus empty and one-key segments."""
+    sizes = [0, 1, 2, 31, 32, 33, 255, 256, 257, 0, 0, 1000, 2047, 2048, 2049, 5000, 1, 70_000, 3, 0, 300]
+    sizes += [int(x) for x in np.random.default_rng(11).integers(0, 400, 1500)]
+    rng = np.random.default_rng(12 if ties else 13)
+    keys, vals = _tile_depth_keys(sizes, rng, ties)
+    end = 31 + int(np.ceil(np.log2(len(sizes))))
+    k, v = gpu_sort(keys, vals, digit_bits=9, end_bit=end, flags=SEG)
+    ek, ev = oracle.sort_pairs(keys, vals)
+    np.testing.assert_array_equal(k, ek)
+    np.testing.assert_array_equal(v, ev)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 4097, 8192 * 3 + 17])
+@pytest.mark.parametrize("kind", ["random", "equal", "sorted", "reversed", "few"])
+def test_segmented_matches_stable_sort(n, kind):
+    """Generic 45-bit keys through the segmented path (capacity large enough
+    for its 2^14 segment starts): 'equal' and 'few' put all keys in one or
+    four segments (the global-memory path)."""
+    rng = np.random.default_rng(n * 5 + len(kind))
+    keys = _keys(kind, n, rng)
+    vals = rng.permutation(n).astype(np.uint32)
+    k, v = gpu_sort(keys, vals, digit_bits=8, end_bit=45, capacity=1 << 16, flags=SEG)
+    ek, ev = oracle.sort_pairs(keys, vals)
+    np.testing.assert_array_equal(k, ek)
+    np.testing.assert_array_equal(v, ev)
+
+
+def test_segmented_begin_bit_and_small_capacity_fallback():
+    """begin_bit > 0 (low bits keep input order), and a capacity too small
+    for the segment starts (ws_sort then runs the full-key passes): both
+    equal the stable sort of the selected bits."""
+    rng = np.random.default_rng(21)
+    keys = rng.integers(0, 2 ** 44, 60_000, dtype=np.uint64)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    perm = np.argsort(keys >> np.uint64(5), kind="stable")
+    k, v = gpu_sort(keys, vals, begin_bit=5, end_bit=44, flags=SEG)
+    np.testing.assert_array_equal(k, keys[perm])
+    np.testing.assert_array_equal(v, vals[perm])
+    small = keys[:300] & np.uint64((1 << 44) - 1)
+    k, v = gpu_sort(small, vals[:300], end_bit=44, flags=SEG)
+    ek, ev = oracle.sort_pairs(small, vals[:300])
+    np.testing.assert_array_equal(k, ek)
+    np.testing.assert_array_equal(v, ev)
+
+
+def test_segmented_sort_of_standard_keys():
+    """The 4,194,304 (tile, depth) keys of the sort benchmark."""
+    keys, vals = S.sort_keys()
+    k, v = gpu_sort(keys, vals, digit_bits=9, end_bit=44, flags=SEG)
     ek, ev = oracle.sort_pairs(keys, vals)
     np.testing.assert_array_equal(k, ek)
     np.testing.assert_array_equal(v, ev)
