@@ -231,7 +231,8 @@ ws_status ws_sort_noalloc(const uint32_t *num_keys, int64_t key_capacity, int32_
  *   image = C + T bg.
  * Inputs: num_keys (device), sorted keys and vals (device), the
  * ws_preprocess outputs. Outputs (device): ranges[tiles][2] uint32 [start,
- * end) of every tile in the sorted list; image[H][W][3]; t_final[H][W]
+ * end) of every tile in the sorted list (start = end for a tile without
+ * pairs); image[H][W][3]; t_final[H][W]
  * (final transmittance); n_contrib[H][W] (1 + list position, relative to
  * the tile's start, of the last splat composited; 0 if none). */
 ws_status ws_rasterize(const uint32_t *num_keys, const uint64_t *keys, const uint32_t *vals,

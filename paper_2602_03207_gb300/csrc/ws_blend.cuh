@@ -11,7 +11,7 @@ constexpr int kBlendBatch = 256;
 // Shared-memory record of one splat for the blend (48 bytes).
 struct SplatRec {
     float4 geo;   // tile-relative centre x, y; conic premultiplied A, B
-    float4 geo2;  // C, opacity, -, -
+    float4 geo2;  // C, log2(opacity), -, -
     float4 col;   // r, g, b, -
 };
 
@@ -67,7 +67,7 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
             r.geo.y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
             r.geo.z = -0.5f * kLog2e * a;
             r.geo.w = -kLog2e * b;
-            r.geo2 = make_float4(-0.5f * kLog2e * c, op, 0.f, 0.f);
+            r.geo2 = make_float4(-0.5f * kLog2e * c, log2f(op), 0.f, 0.f);
             r.col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), 0.f);
             s_rec[j] = r;
             // Box of the ellipse where the alpha reaches 1/255 (§3.4), with a
@@ -97,21 +97,24 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
             for (int base = 0; base < cnt; base += 32) {
                 const int jj = base + lane;
                 uint32_t bits = __ballot_sync(kFull, jj < cnt && ((s_mask[jj] >> blk) & 1u));
+                // Branch-free per splat: a skipped pair adds w = 0, which
+                // leaves C and T bit for bit unchanged.
                 while (bits) {
                     const int j = base + __ffs(bits) - 1;
                     bits &= bits - 1;
                     const float4 geo = s_rec[j].geo;
-                    const float4 geo2 = s_rec[j].geo2;
+                    const float2 geo2 = *reinterpret_cast<const float2*>(&s_rec[j].geo2);
                     const float dx = px[k] - geo.x, dy = py[k] - geo.y;
-                    const float alpha = splat_alpha(dx, dy, geo.z, geo.w, geo2.x, geo2.y);
-                    if (alpha < kAlphaMin) continue;
+                    const float e = splat_log2_alpha(dx, dy, geo.z, geo.w, geo2.x, geo2.y);
+                    const bool keep = e >= kLog2AlphaMin;
+                    const float alpha = fminf(kAlphaMax, ex2_approx(e));
+                    const float w = keep ? alpha * T[k] : 0.f;
                     const float4 col = s_rec[j].col;
-                    const float w = alpha * T[k];
                     C0[k] = fmaf(col.x, w, C0[k]);
                     C1[k] = fmaf(col.y, w, C1[k]);
                     C2[k] = fmaf(col.z, w, C2[k]);
                     T[k] = T[k] - w;
-                    last[k] = start + j + 1 - range.x;
+                    last[k] = keep ? start + j + 1 - range.x : last[k];
                 }
             }
         }
@@ -137,7 +140,7 @@ constexpr int kPart = 9;  // dmean x, y; dconic a, b, c; dsigma; drgb r, g, b
 
 struct BwdRec {
     float4 geo;   // tile-relative centre x, y; premultiplied conic A, B
-    float4 geo2;  // premultiplied C, opacity, conic a, conic b
+    float4 geo2;  // premultiplied C, log2(opacity), conic a, conic b
     float4 col;   // r, g, b, conic c
 };
 
@@ -227,7 +230,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
             r.geo.y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
             r.geo.z = -0.5f * kLog2e * a;
             r.geo.w = -kLog2e * b;
-            r.geo2 = make_float4(-0.5f * kLog2e * c, op, a, b);
+            r.geo2 = make_float4(-0.5f * kLog2e * c, log2f(op), a, b);
             r.col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), c);
             s_rec[j] = r;
             const float det = fmaf(a, c, -b * b);
@@ -273,10 +276,12 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
                     if (!((m >> (warp + k * WARPS)) & 1u)) continue;  // warp-uniform
                     if (pos >= last[k]) continue;
                     const float dx = px[k] - r.geo.x, dy = py[k] - r.geo.y;
-                    const float G = ex2_approx(splat_power2(dx, dy, r.geo.z, r.geo.w, r.geo2.x));
-                    const float raw = __fmul_rn(r.geo2.y, G);
+                    const float e = splat_log2_alpha(dx, dy, r.geo.z, r.geo.w, r.geo2.x, r.geo2.y);
+                    if (!(e >= kLog2AlphaMin)) continue;
+                    const float raw = ex2_approx(e);
                     const float alpha = fminf(kAlphaMax, raw);
-                    if (alpha < kAlphaMin) continue;
+                    // d alpha / d sigma = exp(-q/2) = 2^(e - log2 sigma)
+                    const float G = ex2_approx(e - r.geo2.y);
                     any = true;
                     const float Tb = T[k] / (1.f - alpha);
                     const float w = alpha * Tb;

@@ -141,20 +141,21 @@ constexpr float kLn255 = 5.541263545158426f;
 // sigma < 1/255  <=>  logit < -ln(254)
 constexpr double kOpacityLogitMin = -5.537334267018537;
 
-// Splat alpha at a pixel, from tile-relative offsets and the conic
-// premultiplied by -log2(e)/2 (A, C) and -log2(e) (B):
-//   a = min(0.99, sigma 2^(A dx^2 + B dx dy + C dy^2)).
-// The forward and the backward both call this, so they take the same
-// 1/255 decision bit for bit.
-__device__ __forceinline__ float splat_power2(float dx, float dy, float A, float B, float C) {
-    float u = __fmaf_rn(A, dx, __fmul_rn(B, dy));
-    return __fmaf_rn(dx, u, __fmul_rn(__fmul_rn(C, dy), dy));
+// log2 of the unclamped splat alpha sigma exp(-q/2) at offset (dx, dy) from
+// the centre, with the conic premultiplied (A = -log2(e) a / 2, B = -log2(e) b,
+// C = -log2(e) c / 2) and L = log2(sigma):
+//     e = A dx^2 + B dx dy + C dy^2 + L.
+// A pair is composited iff e >= log2(1/255) (alpha >= 1/255, §3.4's
+// threshold), and then alpha = min(0.99, 2^e). The forward and the backward
+// blend both decide and evaluate through this function, so they agree on
+// every pair.
+constexpr float kLog2AlphaMin = -7.994353436858858f;  // log2(1/255)
+
+__device__ __forceinline__ float splat_log2_alpha(float dx, float dy, float A, float B, float C, float L) {
+    const float u = __fmaf_rn(A, dx, __fmul_rn(B, dy));
+    return __fmaf_rn(dx, u, __fmaf_rn(__fmul_rn(C, dy), dy, L));
 }
 
-__device__ __forceinline__ float splat_alpha(float dx, float dy, float A, float B, float C,
-                                             float opacity) {
-    return fminf(kAlphaMax, __fmul_rn(opacity, ex2_approx(splat_power2(dx, dy, A, B, C))));
-}
 
 // ---------------------------------------------------------------------------
 // Block-wide exclusive scan of one uint32 per thread (THREADS threads).

@@ -27,21 +27,12 @@ namespace {
 
 constexpr int kRangeThreads = 256;
 
-__global__ void __launch_bounds__(kRangeThreads)
-k_zero_ranges(uint2* __restrict__ ranges, uint32_t ntiles) {
-    pdl_wait();
-    pdl_trigger();
-    for (uint32_t t = blockIdx.x * kRangeThreads + threadIdx.x; t < ntiles; t += gridDim.x * kRangeThreads)
-        ranges[t] = make_uint2(0u, 0u);
-}
-
-// ranges[t] = [start, end) of tile t in the sorted key list. Tiles with no
-// pairs keep the zero range written by k_zero_ranges. Each warp takes
-// kRangeUnroll consecutive chunks of 32 keys per step, all loads issued
-// before any is used; the next key comes from the neighbour lane (the
-// warp's last lane loads the one past the chunk).
-constexpr int kRangeUnroll = 8;
-
+// ranges[t] = [start, end) of tile t in the sorted key list, for every tile
+// (an empty tile gets start = end), in one pass over positions 0..n: at
+// position i, between the tiles a of key i-1 and c of key i, tiles a+1..c
+// start and tiles a..c-1 end. The warp fills its lanes' runs of tiles
+// together, so a long run of empty tiles does not serialise one thread.
+// Keys whose tile is >= ntiles (none in a frame) count as past the end.
 __global__ void __launch_bounds__(kRangeThreads)
 k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys,
               uint2* __restrict__ ranges, uint32_t ntiles) {
@@ -49,26 +40,25 @@ k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ nu
     pdl_trigger();
     const uint32_t n = *num_keys;
     const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (kRangeThreads / 32);
-    const uint32_t gw = blockIdx.x * (kRangeThreads / 32) + (threadIdx.x >> 5);
-    for (uint32_t base = gw * 32 * kRangeUnroll; base < n; base += warps * 32 * kRangeUnroll) {
-        uint32_t t[kRangeUnroll], tn[kRangeUnroll];
-#pragma unroll
-        for (int u = 0; u < kRangeUnroll; ++u) {
-            const uint32_t p = base + u * 32 + lane;
-            t[u] = p < n ? (uint32_t)(__ldg(keys + p) >> 31) : 0xffffffffu;
-            tn[u] = (lane == 31 && p + 1 < n) ? (uint32_t)(__ldg(keys + p + 1) >> 31) : 0xffffffffu;
-        }
-#pragma unroll
-        for (int u = 0; u < kRangeUnroll; ++u) {
-            const uint32_t p = base + u * 32 + lane;
-            uint32_t next = __shfl_down_sync(kFull, t[u], 1);
-            if (lane == 31) next = tn[u];
-            if (p >= n || t[u] >= ntiles) continue;  // past the count / not a key of this grid
-            if (p == 0) ranges[t[u]].x = 0;
-            if (t[u] != next) {
-                ranges[t[u]].y = p + 1;
-                if (p + 1 < n && next < ntiles) ranges[next].x = p + 1;
+    const int64_t stride = (int64_t)gridDim.x * kRangeThreads;
+    for (int64_t base = (int64_t)blockIdx.x * kRangeThreads + (threadIdx.x & ~31); base <= (int64_t)n;
+         base += stride) {
+        const int64_t i = base + lane;
+        int64_t c = (int64_t)ntiles;
+        if (i < (int64_t)n) c = min((int64_t)(__ldg(keys + i) >> 31), (int64_t)ntiles);
+        int64_t a = __shfl_up_sync(kFull, c, 1);
+        if (lane == 0) a = i == 0 ? -1 : min((int64_t)(__ldg(keys + i - 1) >> 31), (int64_t)ntiles);
+        if (i == 0) a = -1;
+        if (i > (int64_t)n) a = c;  // past the count: nothing to write
+        uint32_t todo = __ballot_sync(kFull, c > a);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t lo = __shfl_sync(kFull, a, src), hi = __shfl_sync(kFull, c, src);
+            const uint32_t pos = (uint32_t)__shfl_sync(kFull, (uint32_t)i, src);
+            for (int64_t t = lo + lane; t <= hi; t += kWarp) {
+                if (t >= 0 && t < hi && t < (int64_t)ntiles) ranges[t].y = pos;
+                if (t > lo && t < (int64_t)ntiles) ranges[t].x = pos;
             }
         }
     }
@@ -93,9 +83,7 @@ cudaError_t launch_tile_ranges(const uint64_t* keys, const uint32_t* num_keys, u
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     uint2* r2w = reinterpret_cast<uint2*>(ranges);
-    cudaError_t e = launch_pdl(k_zero_ranges, dim3(sms), dim3(kRangeThreads), 0, stream, r2w, ntiles);
-    if (e != cudaSuccess) return e;
-    return launch_pdl(k_tile_ranges, dim3(sms * 4), dim3(kRangeThreads), 0, stream, keys, num_keys, r2w, ntiles);
+    return launch_pdl(k_tile_ranges, dim3(sms * 8), dim3(kRangeThreads), 0, stream, keys, num_keys, r2w, ntiles);
 }
 
 cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t /*key_capacity_hint*/,
