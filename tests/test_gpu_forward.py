@@ -36,14 +36,18 @@ def _check_preprocess(g, ref, n_amb_max=None):
     vv = vis_ref & vis_gpu
     np.testing.assert_allclose(g["mean2d"][vv], p["mean2d"][vv], rtol=0, atol=2e-6)
     # conic: what the blend uses is the quadratic form q = d^T Q d; its
-    # relative error over all directions d is the spectral radius of
-    # Sigma'_ref (Q_gpu - Q_ref), bounded here by 1e-4.
+    # relative error r over all directions d is the spectral radius of
+    # Sigma'_ref (Q_gpu - Q_ref). It moves alpha = sigma exp(-q/2) by at most
+    # sigma (q/2) e^{-q/2} r <= 0.37 sigma r (largest at q = 2), so r <= 5e-4
+    # keeps every pixel inside the 2e-4 image bound. (FP32 inversion of an
+    # elongated Sigma' loses about eps * Sigma'_xx Sigma'_yy / det: 1.6e-4 for
+    # the worst of the 3.8M splats of the 4K workload.)
     cov = p["cov2d"][vv]
     dq = g["conic"][vv].astype(np.float64) - p["conic"][vv]
     S2 = np.stack([np.stack([cov[:, 0], cov[:, 1]], -1), np.stack([cov[:, 1], cov[:, 2]], -1)], -2)
     D2 = np.stack([np.stack([dq[:, 0], dq[:, 1]], -1), np.stack([dq[:, 1], dq[:, 2]], -1)], -2)
     metric = np.abs(np.linalg.eigvals(S2 @ D2)).max(-1)
-    assert metric.max() <= 1e-4, metric.max()
+    assert metric.max() <= 5e-4, metric.max()
     np.testing.assert_allclose(g["rgb"][vv], p["rgb"][vv], rtol=0, atol=2e-6)
     np.testing.assert_allclose(g["opacity"][vv], p["opacity"][vv], rtol=2e-6, atol=0)
     if n_amb_max is not None:
@@ -188,6 +192,34 @@ def test_hd_workload_sampled():
     _check_emission(g, ref)
     _check_sort(g)
     mask = np.zeros((1080, 1920), bool)
+    for t in tiles:
+        y0, x0 = (t // tx) * 16, (t % tx) * 16
+        mask[y0:y0 + 16, x0:x0 + 16] = True
+    st = compare_image(g, ref, tile_mask=mask)
+    assert st["n_bad"] == 0, st
+    assert st["n_multi"] <= 0.001 * st["n_pix"]
+
+
+def test_uhd_workload_sampled():
+    """The 6,000,000-Gaussian 3840x2160 workload (pose 3, whose densest tile
+    holds 4,389 pairs: the segmented sort's global-memory path): every
+    Gaussian's pre-processing, the whole pair list and sort, and the image on
+    the densest 32 plus 64 seeded tiles against the oracle."""
+    scene = S.uhd_scene()
+    cam = S.uhd_camera(3)
+    r = gpu_frame(scene, cam)
+    g = fetch(r)
+    tx, ty = (3840 + 15) // 16, (2160 + 15) // 16
+    counts = g["ranges"][:, 1] - g["ranges"][:, 0]
+    assert counts.max() > 2048
+    dense = np.argsort(-counts, kind="stable")[:32]
+    rng = np.random.default_rng(78)
+    tiles = np.unique(np.concatenate([dense, rng.choice(tx * ty, 64, replace=False)]))
+    ref = oracle.render(scene, cam, tile_list=tiles)
+    _check_preprocess(g, ref, n_amb_max=int(0.005 * len(scene["means"])))
+    _check_emission(g, ref)
+    _check_sort(g)
+    mask = np.zeros((2160, 3840), bool)
     for t in tiles:
         y0, x0 = (t // tx) * 16, (t % tx) * 16
         mask[y0:y0 + 16, x0:x0 + 16] = True
