@@ -279,3 +279,18 @@ def test_sort_variants_give_identical_frames():
     for sort in ("lsd", "lookback"):
         for a, b in zip(out["segmented"], out[sort]):
             np.testing.assert_array_equal(a, b)
+
+
+def test_ply_scene_renders_like_the_original(tmp_path):
+    """A scene written to and read back from a 3DGS PLY file renders the
+    same frame as the in-memory scene, within the oracle's bar."""
+    from paper_2602_03207_gb300 import ply
+    scene, cam = S.small_forward()
+    path = tmp_path / "scene.ply"
+    ply.save_ply(path, scene)
+    loaded = ply.load_ply(path)
+    a = fetch(gpu_frame(loaded, cam))
+    b = fetch(gpu_frame(scene, cam))
+    np.testing.assert_array_equal(a["image"], b["image"])
+    st = compare_image(a, oracle.render(loaded, cam))
+    assert st["n_bad"] == 0, st
