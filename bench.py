@@ -297,6 +297,54 @@ def ablation_table(scene, cams, tile, digit_bits, dev, frames=40):
     return out
 
 
+def packed_variant(scene, cams, tile, digit_bits, key_capacity, dev, steps=1000):
+    """The packed-record variant (§3.2: RGBA8 colour + opacity, binary16
+    ellipse axes) on the same frames: frames/s timed like the headline (no
+    events between stages), plus per-stage times from a separate run."""
+    import torch
+    from paper_2602_03207_gb300 import capi, render
+    n = scene["means"].shape[0]
+    W, H = cams[0]["width"], cams[0]["height"]
+    r = render.Renderer(n, W, H, tile=tile, digit_bits=digit_bits, key_capacity=key_capacity, device=dev,
+                        packed=True)
+    ccams = [capi.camera(c) for c in cams]
+    for i in range(10):
+        r.forward(scene, cams[i % len(cams)])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(steps):
+        cam = ccams[i % len(cams)]
+        r.preprocess(scene, cam)
+        r.cull(cam)
+        r.sort()
+        r.rasterize(cam)
+    b.record()
+    torch.cuda.synchronize()
+    r.check_status()
+    ms = a.elapsed_time(b) / steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(200)]
+    for i in range(200):
+        cam = ccams[i % len(cams)]
+        e = ev[i]
+        e[0].record()
+        r.preprocess(scene, cam)
+        e[1].record()
+        r.cull(cam)
+        e[2].record()
+        r.sort()
+        e[3].record()
+        r.rasterize(cam)
+        e[4].record()
+    torch.cuda.synchronize()
+    st = {s: sum(e[j].elapsed_time(e[j + 1]) for e in ev) / 200 for j, s in enumerate(STAGES)}
+    del r
+    torch.cuda.empty_cache()
+    return {"value": round(1e3 / ms, 2), "unit": "frames/s", "ms_per_step": round(ms, 4), "steps": steps,
+            "stages_ms": {k: round(v, 4) for k, v in st.items()},
+            "record_bytes_per_splat": {"packed": 20, "float": 44}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -506,6 +554,8 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
         "clocks": clocks,
     }
     out["sort_only"] = sort_only(r.image.device, digit_bits=args.digit_bits)
+    out["packed_variant"] = packed_variant(scene, cams, r.tile, args.digit_bits, r.key_capacity, r.image.device,
+                                           steps=min(args.steps, 1000))
     if not args.no_ablation:
         out["ablation"] = ablation_table(scene, cams, r.tile, args.digit_bits, r.image.device,
                                          frames=40 if args.workload == "hd" else 16)

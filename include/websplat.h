@@ -241,6 +241,36 @@ ws_status ws_rasterize(const uint32_t *num_keys, const uint64_t *keys, const uin
                        uint32_t *ranges, float *image, float *t_final, uint32_t *n_contrib,
                        void *stream);
 
+/* Packed-record variant of ws_preprocess (§3.2 packs each splat's colour and
+ * opacity into one RGBA8 word and its ellipse axes into two words of
+ * binary16 halves). Same inputs and the same culling as ws_preprocess; per
+ * visible splat it writes instead:
+ *   mean2d[n][2]  float32 centre (px)
+ *   axes[n][2]    uint32: (v1.x | v1.y << 16), (v2.x | v2.y << 16) as IEEE
+ *                 binary16, the major and minor axes sqrt(l) e of Sigma'
+ *                 (Sigma' = v1 v1^T + v2 v2^T), rounded to nearest even
+ *   rgba[n]       uint32: r | g << 8 | b << 16 | sigma << 24, each
+ *                 round(255 clamp(x, 0, 1)) (colours above 1 are clamped)
+ * and depth, rect and tiles_touched as ws_preprocess, with the extent, the
+ * viewport test and the tile rectangle computed from the packed sigma and
+ * axes. ws_cull and ws_sort take the outputs unchanged; ws_rasterize_packed
+ * reads the packed record. Images differ from the float path by the
+ * quantisation (at most about 1/255 per channel where no colour exceeds 1).
+ * All pointers device, 16-byte aligned; errors as ws_preprocess. */
+ws_status ws_preprocess_packed(int64_t n, const float *means, const float *log_scales, const float *quats,
+                               const float *opacity_logits, const float *sh, const ws_camera *cam,
+                               const ws_config *cfg, float *mean2d, uint32_t *axes, uint32_t *rgba,
+                               float *depth, uint16_t *rect, uint32_t *tiles_touched, void *stream);
+
+/* ws_rasterize on the packed record of ws_preprocess_packed: the blend
+ * rebuilds Sigma' from the two axes (det = (v1 x v2)^2), inverts it and
+ * decodes colour and sigma from the RGBA8 word; everything else (tile
+ * ranges, compositing, outputs, errors) is ws_rasterize's. */
+ws_status ws_rasterize_packed(const uint32_t *num_keys, const uint64_t *keys, const uint32_t *vals,
+                              const float *mean2d, const uint32_t *axes, const uint32_t *rgba,
+                              const ws_camera *cam, const ws_config *cfg, uint32_t *ranges, float *image,
+                              float *t_final, uint32_t *n_contrib, void *stream);
+
 /* Backward of the whole frame for a loss L(image): given d_image = dL/dimage
  * (device, [H][W][3]), writes dL/d(means, log_scales, quats, opacity_logits,
  * sh) (device, the input layouts; zero for culled Gaussians). The paper has

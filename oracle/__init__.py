@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 DEFAULTS = {"tile": 16, "dilation": 0.3, "guard": 1.3, "amb_px_rel": 1e-6, "amb_alpha": 1e-4, "flags": 0}
-NO_OPACITY_CULL, NO_AABB_CULL, FIXED_RADIUS = 1, 2, 8
+NO_OPACITY_CULL, NO_AABB_CULL, FIXED_RADIUS, PACKED = 1, 2, 8, 16
 REASONS = {0: "visible", 1: "opacity", 2: "quat", 3: "near", 4: "det", 5: "offscreen"}
 
 
@@ -85,6 +85,9 @@ def lib():
             L.or_loss_grad.argtypes = [C.c_int64, _D, _D, _D, _D, _D, C.POINTER(_Camera),
                                        C.POINTER(_Config), _D, _D, _D, _D, _D, _D, _D, _U64]
             L.or_loss_grad.restype = C.c_double
+            L.or_round_f16.argtypes = [C.c_double]
+            L.or_round_f16.restype = C.c_double
+            L.or_axes.argtypes = [C.c_double, C.c_double, C.c_double, _D, _D]
             _lib = L
     return _lib
 
@@ -95,6 +98,22 @@ def _p(a, t):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def round_f16(x):
+    """Nearest IEEE binary16 value of each double, ties to even (§3.2's
+    packed axes)."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.vectorize(lambda v: lib().or_round_f16(float(v)), otypes=[np.float64])(x)
+
+
+def axes(sxx, sxy, syy):
+    """Major and minor ellipse axes (v1, v2) of a 2D covariance, with
+    v1 v1^T + v2 v2^T = [[sxx, sxy], [sxy, syy]] (§3.2's packed axes)."""
+    v1 = np.zeros(2)
+    v2 = np.zeros(2)
+    lib().or_axes(float(sxx), float(sxy), float(syy), _p(v1, _D), _p(v2, _D))
+    return v1, v2
 
 
 def camera(cam):

@@ -19,6 +19,11 @@
  *                       projection + AABB culling + 32-bit float depth,
  *                       §3.4 opacity culling (sigma < 1/255) and the
  *                       opacity-aware extent (1/255 = sigma e^{-r^2}).
+ *                       With OR_PACKED, the record is packed first (§3.2):
+ *                       opacity and clamped colour on 8 bits, the centre in
+ *                       float32, the ellipse as two binary16 axes
+ *                       (or_round_f16, or_axes), and Sigma', the conic and
+ *                       the extent follow from the packed values.
  *   or_emit_keys        the <tile, splat> pair list of §3.4 (the CUDA-style
  *                       tile decomposition), one key per overlapped tile.
  *   or_sort_pairs       §3.3.2: a stable sort (elements with equal keys keep
@@ -84,10 +89,11 @@ typedef struct {
     double guard;        /* frustum guard factor of the Jacobian clamp */
     double amb_px_rel;   /* relative margin of tile-bound / viewport decisions */
     double amb_alpha;    /* relative margin of the per-pixel 1/255 decision */
-    int32_t flags;       /* ablations (§4.4): 1 keep sigma < 1/255, 2 keep off-screen boxes, 8 fixed extent */
+    int32_t flags;       /* ablations (§4.4): 1 keep sigma < 1/255, 2 keep off-screen boxes, 8 fixed extent;
+                            16 packed record (§3.2) */
 } or_config;
 
-enum { OR_NO_OPACITY_CULL = 1, OR_NO_AABB_CULL = 2, OR_FIXED_RADIUS = 8 };
+enum { OR_NO_OPACITY_CULL = 1, OR_NO_AABB_CULL = 2, OR_FIXED_RADIUS = 8, OR_PACKED = 16 };
 
 enum { OR_VISIBLE = 0, OR_CULL_OPACITY = 1, OR_CULL_QUAT = 2, OR_CULL_NEAR = 3,
        OR_CULL_DET = 4, OR_CULL_OFFSCREEN = 5 };
@@ -211,6 +217,52 @@ float or_depth32(const double X[3], const double viewmat[12])
 
 static double tau_opacity(void) { return -log(254.0); } /* sigma < 1/255 <=> logit < -ln 254 */
 
+/* ----------------------------------------------------------- packed record
+ * §3.2 packs a splat's colour and opacity into one RGBA8 word and its
+ * ellipse axes into two words of two IEEE binary16 halves each. */
+
+/* Round to the nearest binary16 value, ties to even, from double directly
+ * (no intermediate float). Overflow gives +-inf. */
+double or_round_f16(double x)
+{
+    if (x == 0.0 || isnan(x) || isinf(x)) return x;
+    double ax = fabs(x);
+    int e;
+    frexp(ax, &e);                      /* ax = f 2^e, f in [0.5, 1) */
+    int ulp_exp = e - 11;               /* 11 significant bits */
+    if (ulp_exp < -24) ulp_exp = -24;   /* subnormal halves: spacing 2^-24 */
+    double q = ldexp(rint(ldexp(ax, -ulp_exp)), ulp_exp);
+    if (q >= 65520.0) q = INFINITY;     /* 65520 rounds up past the largest half, 65504 */
+    return x < 0 ? -q : q;
+}
+
+/* x in [0, 1] on 8 bits: the nearest multiple of 1/255, ties to even. */
+static double quant8(double x)
+{
+    if (x < 0.0) x = 0.0;
+    if (x > 1.0) x = 1.0;
+    return rint(x * 255.0) / 255.0;
+}
+
+/* Ellipse axes of the 2D covariance [[sxx, sxy], [sxy, syy]]: v1 = sqrt(l1) e1
+ * (major), v2 = sqrt(l2) e2 (minor, e2 = e1 turned by +90 degrees), so that
+ * Sigma' = v1 v1^T + v2 v2^T. e1 comes from whichever row of (Sigma' - l1 I)
+ * is better conditioned; l2 = det / l1 avoids the cancellation of m - d. */
+void or_axes(double sxx, double sxy, double syy, double *v1, double *v2)
+{
+    double m = 0.5 * (sxx + syy), h = 0.5 * (sxx - syy);
+    double d = sqrt(h * h + sxy * sxy);
+    double l1 = m + d, l2 = (sxx * syy - sxy * sxy) / l1;
+    double ex = 1.0, ey = 0.0;
+    if (d > 0.0) {
+        if (h >= 0.0) { double nn = hypot(d + h, sxy); ex = (d + h) / nn; ey = sxy / nn; }
+        else { double nn = hypot(sxy, d - h); ex = sxy / nn; ey = (d - h) / nn; }
+    }
+    double r1 = sqrt(l1), r2 = sqrt(l2);
+    v1[0] = r1 * ex; v1[1] = r1 * ey;
+    v2[0] = -r2 * ey; v2[1] = r2 * ex;
+}
+
 static double flr(double v) { return floor(v); }
 
 /* ------------------------------------------------------------ preprocess */
@@ -318,6 +370,28 @@ int64_t or_preprocess(int64_t n, const double *means, const double *log_scales,
             for (int k = 0; k < 16; ++k) acc += Y[k] * sh[(16 * i + k) * 3 + ch];
             acc += 0.5;
             rgb[3 * i + ch] = acc > 0.0 ? acc : 0.0;
+        }
+
+        if (cfg->flags & OR_PACKED) {
+            /* Packed record (§3.2): opacity and clamped colour on 8 bits, the
+             * centre in float32, the ellipse as two binary16 axes; Sigma',
+             * the conic and the extent below follow from the packed values. */
+            sigma = quant8(sigma);
+            opacity[i] = sigma;
+            for (int ch = 0; ch < 3; ++ch) rgb[3 * i + ch] = quant8(rgb[3 * i + ch]);
+            mx = (double)(float)mx; my = (double)(float)my;
+            mean2d[2 * i] = mx; mean2d[2 * i + 1] = my;
+            double v1[2], v2[2];
+            or_axes(sxx, sxy, syy, v1, v2);
+            for (int a = 0; a < 2; ++a) { v1[a] = or_round_f16(v1[a]); v2[a] = or_round_f16(v2[a]); }
+            sxx = v1[0] * v1[0] + v2[0] * v2[0];
+            sxy = v1[0] * v1[1] + v2[0] * v2[1];
+            syy = v1[1] * v1[1] + v2[1] * v2[1];
+            double cross = v1[0] * v2[1] - v1[1] * v2[0];
+            det = cross * cross;
+            cov2d[3 * i] = sxx; cov2d[3 * i + 1] = sxy; cov2d[3 * i + 2] = syy;
+            if (!(det > 0.0)) { reason[i] = OR_CULL_DET; continue; }
+            conic[3 * i] = syy / det; conic[3 * i + 1] = -sxy / det; conic[3 * i + 2] = sxx / det;
         }
 
         /* Opacity-aware extent (§3.4): a >= 1/255 <=> q <= q_c = 2 ln(255 sigma).

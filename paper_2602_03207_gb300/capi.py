@@ -88,6 +88,8 @@ def lib():
             L.ws_cull.argtypes = [I64, P, P, P, cam_p, cfg_p, P, P, P, I64, P, P, P]
             L.ws_sort.argtypes = [P, I64, I32, I32, P, P, P, P, cfg_p, P, C.POINTER(I32), P]
             L.ws_rasterize.argtypes = [P, P, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
+            L.ws_preprocess_packed.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P]
+            L.ws_rasterize_packed.argtypes = [P, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
             L.ws_rasterize_backward.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P, P, P,
                                                 P, P, P, I64, P, P, P, P, P, P, P]
             L.ws_sort_test_stalled_tile.argtypes = [P, I64, I32, I32, P, P, P, P, cfg_p, P, I32, C.POINTER(I32), P]
@@ -195,6 +197,21 @@ def ws_rasterize(num_keys, keys, vals, mean2d, conic, opacity, rgb, cam, cfg, ra
         _ptr(num_keys), _ptr(keys), _ptr(vals), _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb),
         C.byref(cam), C.byref(cfg), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib),
         _stream(stream)))
+
+
+def ws_preprocess_packed(n, means, log_scales, quats, opacity_logits, sh, cam, cfg, mean2d, axes, rgba, depth,
+                         rect, tiles_touched, stream=None):
+    _check("ws_preprocess_packed", lib().ws_preprocess_packed(
+        int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh), C.byref(cam),
+        C.byref(cfg), _ptr(mean2d), _ptr(axes), _ptr(rgba), _ptr(depth), _ptr(rect), _ptr(tiles_touched),
+        _stream(stream)))
+
+
+def ws_rasterize_packed(num_keys, keys, vals, mean2d, axes, rgba, cam, cfg, ranges, image, t_final, n_contrib,
+                        stream=None):
+    _check("ws_rasterize_packed", lib().ws_rasterize_packed(
+        _ptr(num_keys), _ptr(keys), _ptr(vals), _ptr(mean2d), _ptr(axes), _ptr(rgba), C.byref(cam),
+        C.byref(cfg), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib), _stream(stream)))
 
 
 def ws_rasterize_backward(n, means, log_scales, quats, opacity_logits, sh, cam, cfg, mean2d, conic, rgb,

@@ -271,6 +271,36 @@ ws_status ws_rasterize(const uint32_t* num_keys, const uint64_t* keys, const uin
                                             image, t_final, n_contrib, static_cast<cudaStream_t>(stream)));
 }
 
+ws_status ws_preprocess_packed(int64_t n, const float* means, const float* log_scales, const float* quats,
+                               const float* opacity_logits, const float* sh, const ws_camera* cam,
+                               const ws_config* cfg, float* mean2d, uint32_t* axes, uint32_t* rgba, float* depth,
+                               uint16_t* rect, uint32_t* tiles_touched, void* stream) {
+    if (n < 0 || n >= (int64_t(1) << 32) || !valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
+    if (n == 0) return WS_OK;
+    const void* ptrs[] = {means, log_scales, quats, opacity_logits, sh, mean2d, axes, rgba, depth, rect,
+                          tiles_touched};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    const Frame f = make_frame(cam, cfg);
+    if (f.TX > 65535 || f.TY > 65535) return WS_ERR_UNSUPPORTED;
+    return cuda_status(ws::launch_preprocess_packed(n, means, log_scales, quats, opacity_logits, sh, f, mean2d, axes,
+                                                    rgba, depth, rect, tiles_touched,
+                                                    static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_rasterize_packed(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals,
+                              const float* mean2d, const uint32_t* axes, const uint32_t* rgba, const ws_camera* cam,
+                              const ws_config* cfg, uint32_t* ranges, float* image, float* t_final,
+                              uint32_t* n_contrib, void* stream) {
+    if (!valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, keys, vals, mean2d, axes, rgba, ranges, image, t_final, n_contrib};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    const Frame f = make_frame(cam, cfg);
+    return cuda_status(ws::launch_rasterize_packed(num_keys, keys, vals, mean2d, axes, rgba, f, ranges, image,
+                                                   t_final, n_contrib, static_cast<cudaStream_t>(stream)));
+}
+
 ws_status ws_rasterize_backward(int64_t n, const float* means, const float* log_scales,
                                 const float* quats, const float* opacity_logits, const float* sh,
                                 const ws_camera* cam, const ws_config* cfg, const float* mean2d,

@@ -112,8 +112,9 @@ k_blend_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ val
     const uint32_t t = blockIdx.x;
     const int v = view_of_tile(ft.tile_off, ft.views, t);
     const uint64_t vo = (uint64_t)v * (uint64_t)n, po = ft.pix_off[v];
-    blend_tile<TS>(ft.f[v], (int)(t - ft.tile_off[v]), ranges[t], vals, mean2d + vo, conic + 3 * vo, opacity,
-                   rgb + 3 * vo, image + 3 * po, t_final + po, n_contrib + po);
+    const FloatSplats sp{mean2d + vo, conic + 3 * vo, opacity, rgb + 3 * vo};
+    blend_tile<TS>(ft.f[v], (int)(t - ft.tile_off[v]), ranges[t], vals, sp, image + 3 * po, t_final + po,
+                   n_contrib + po);
 }
 
 template <int TS>

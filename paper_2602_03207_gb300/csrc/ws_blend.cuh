@@ -15,17 +15,36 @@ struct SplatRec {
     float4 col;   // r, g, b, -
 };
 
+// Per-splat inputs of the blend, read from the float outputs of
+// ws_preprocess: the double-float centre (made tile-relative without
+// large-magnitude rounding), the conic (a, b, c), sigma and the colour.
+struct FloatSplats {
+    const float4* __restrict__ mean2d;
+    const float* __restrict__ conic;
+    const float* __restrict__ opacity;
+    const float* __restrict__ rgb;
+    __device__ __forceinline__ void load(uint32_t g, float ox, float oy, float& x, float& y, float& a, float& b,
+                                         float& c, float& op, float4& col) const {
+        const float4 m = __ldg(mean2d + g);
+        x = __fadd_rn(__fsub_rn(m.x, ox), m.z);
+        y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
+        a = __ldg(conic + 3 * g);
+        b = __ldg(conic + 3 * g + 1);
+        c = __ldg(conic + 3 * g + 2);
+        op = __ldg(opacity + g);
+        col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), 0.f);
+    }
+};
+
 // One block per tile. Each warp owns WPB (TS^2/256, at least 1) 8x4 pixel
 // blocks. Splats are staged 256 at a time; while staging, every splat also
 // records the bitmask of the tile's 8x4 blocks that its opacity-aware
 // extent box reaches. Each warp then walks the batch 32 splats at a time,
 // ballots the bit of its own block and visits only those splats, in list
 // order, so per pixel the compositing order is unchanged.
-template <int TS>
+template <int TS, typename Splats>
 __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
-                                           const float4* __restrict__ mean2d, const float* __restrict__ conic,
-                                           const float* __restrict__ opacity, const float* __restrict__ rgb,
-                                           float* __restrict__ image, float* __restrict__ t_final,
+                                           const Splats& sp, float* __restrict__ image, float* __restrict__ t_final,
                                            uint32_t* __restrict__ n_contrib) {
     constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
     constexpr int WARPS = THREADS / 32;
@@ -59,16 +78,12 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += THREADS) {
             const uint32_t g = __ldg(vals + start + j);
-            const float4 m = __ldg(mean2d + g);
-            const float a = __ldg(conic + 3 * g), b = __ldg(conic + 3 * g + 1), c = __ldg(conic + 3 * g + 2);
-            const float op = __ldg(opacity + g);
+            float a, b, c, op;
             SplatRec r;
-            r.geo.x = __fadd_rn(__fsub_rn(m.x, ox), m.z);
-            r.geo.y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
+            sp.load(g, ox, oy, r.geo.x, r.geo.y, a, b, c, op, r.col);
             r.geo.z = -0.5f * kLog2e * a;
             r.geo.w = -kLog2e * b;
             r.geo2 = make_float4(-0.5f * kLog2e * c, log2f(op), 0.f, 0.f);
-            r.col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), 0.f);
             s_rec[j] = r;
             // Box of the ellipse where the alpha reaches 1/255 (§3.4), with a
             // small margin so rounding never drops a pair the per-pixel test

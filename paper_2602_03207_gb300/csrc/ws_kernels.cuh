@@ -64,6 +64,16 @@ cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t key_capacity_hint
                              const Frame& f, uint32_t* ranges, float* image, float* t_final,
                              uint32_t* n_contrib, cudaStream_t stream);
 
+// ---- packed-record variant
+cudaError_t launch_preprocess_packed(int64_t n, const float* means, const float* log_scales, const float* quats,
+                                     const float* logits, const float* sh, const Frame& f, float* mean2d,
+                                     uint32_t* axes, uint32_t* rgba, float* depth, uint16_t* rect,
+                                     uint32_t* tiles_touched, cudaStream_t stream);
+cudaError_t launch_rasterize_packed(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals,
+                                    const float* mean2d, const uint32_t* axes, const uint32_t* rgba, const Frame& f,
+                                    uint32_t* ranges, float* image, float* t_final, uint32_t* n_contrib,
+                                    cudaStream_t stream);
+
 // ---- backward
 size_t backward_scratch_bytes(int64_t key_capacity);
 cudaError_t launch_backward(int64_t n, const float* means, const float* log_scales, const float* quats,

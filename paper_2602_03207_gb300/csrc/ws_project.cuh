@@ -81,12 +81,11 @@ struct Projection {
 // Projection of one Gaussian that passed the opacity and near-plane tests:
 // Sigma = M M^T with M = R(q) diag(exp(log_scale)) (§2.1); the centre through
 // the pinhole in double-float; Sigma' = V V^T + dilation I with V = J W M
-// (EWA Jacobian J with the guard-band clamp); conic = Sigma'^{-1}; the
-// opacity-aware extent e = sqrt(2 ln(255 sigma) diag Sigma') (§3.4); the
-// viewport AABB test (§3.2) and the tile rectangle. Returns false when the
-// quaternion is zero, Sigma' is degenerate or the box misses the viewport.
-__device__ __forceinline__ bool project_splat(const Frame& f, float x, float y, float z, float4 q, float l0,
-                                              float l1, float l2, float logit, Projection& P) {
+// (EWA Jacobian J with the guard-band clamp) returned in sxx, sxy, syy;
+// conic = Sigma'^{-1}. Returns false when the quaternion is zero or Sigma' is
+// degenerate.
+__device__ __forceinline__ bool project_core(const Frame& f, float x, float y, float z, float4 q, float l0, float l1,
+                                             float l2, Projection& P, float& sxx, float& sxy, float& syy) {
     const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
     if (qn2 == 0.f) return false;
     const float inv = rsqrtf(qn2);
@@ -119,24 +118,25 @@ __device__ __forceinline__ bool project_splat(const Frame& f, float x, float y, 
         V0[k] = T0[0] * M[k] + T0[1] * M[3 + k] + T0[2] * M[6 + k];
         V1[k] = T1[0] * M[k] + T1[1] * M[3 + k] + T1[2] * M[6 + k];
     }
-    const float sxx = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2] + f.dilation;
-    const float sxy = V0[0] * V1[0] + V0[1] * V1[1] + V0[2] * V1[2];
-    const float syy = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2] + f.dilation;
+    sxx = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2] + f.dilation;
+    sxy = V0[0] * V1[0] + V0[1] * V1[1] + V0[2] * V1[2];
+    syy = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2] + f.dilation;
     const float det = fmaf(sxx, syy, -sxy * sxy);
     if (!(det > 0.f)) return false;
     const float id = 1.f / det;
     P.ca = syy * id;
     P.cb = -sxy * id;
     P.cc = sxx * id;
-    // sigma and the opacity-aware extent (§3.4): q_c = 2 ln(255 sigma)
-    const float en = expf(-logit);
-    P.sigma = 1.f / (1.f + en);
-    // WS_CFG_FIXED_RADIUS (ablation): the box every splat would need at
-    // sigma = 1, independent of its opacity (conservative, only larger).
-    const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, 2.f * (kLn255 - log1pf(en)));
-    const float ex = sqrtf(qc * sxx), ey = sqrtf(qc * syy);
-    const float lox = __fadd_rn(__fsub_rn(mx.hi, ex), mx.lo), hix = __fadd_rn(__fadd_rn(mx.hi, ex), mx.lo);
-    const float loy = __fadd_rn(__fsub_rn(my.hi, ey), my.lo), hiy = __fadd_rn(__fadd_rn(my.hi, ey), my.lo);
+    return true;
+}
+
+// Viewport AABB test (§3.2) of the box [m - e, m + e] (the centre m as
+// double-float hi + lo) and its tile rectangle. Returns false when the box
+// misses the viewport (unless WS_CFG_NO_AABB_CULL keeps it, clamped).
+__device__ __forceinline__ bool splat_rect(const Frame& f, float mxh, float mxl, float myh, float myl, float ex,
+                                           float ey, Projection& P) {
+    const float lox = __fadd_rn(__fsub_rn(mxh, ex), mxl), hix = __fadd_rn(__fadd_rn(mxh, ex), mxl);
+    const float loy = __fadd_rn(__fsub_rn(myh, ey), myl), hiy = __fadd_rn(__fadd_rn(myh, ey), myl);
     const bool on = hix >= 0.f && lox < (float)f.W && hiy >= 0.f && loy < (float)f.H;
     if (!on && !(f.flags & WS_CFG_NO_AABB_CULL)) return false;
     const float its = 1.f / (float)f.TS;  // exact: TS is a power of two
@@ -145,6 +145,22 @@ __device__ __forceinline__ bool project_splat(const Frame& f, float x, float y, 
     P.y0 = (uint32_t)fminf((float)(f.TY - 1), fmaxf(0.f, floorf(loy * its)));
     P.y1 = (uint32_t)fminf((float)(f.TY - 1), fmaxf(0.f, floorf(hiy * its)));
     return true;
+}
+
+// project_core, then sigma and the opacity-aware extent
+// e = sqrt(2 ln(255 sigma) diag Sigma') (§3.4) and splat_rect.
+__device__ __forceinline__ bool project_splat(const Frame& f, float x, float y, float z, float4 q, float l0,
+                                              float l1, float l2, float logit, Projection& P) {
+    float sxx, sxy, syy;
+    if (!project_core(f, x, y, z, q, l0, l1, l2, P, sxx, sxy, syy)) return false;
+    // sigma and the opacity-aware extent (§3.4): q_c = 2 ln(255 sigma)
+    const float en = expf(-logit);
+    P.sigma = 1.f / (1.f + en);
+    // WS_CFG_FIXED_RADIUS (ablation): the box every splat would need at
+    // sigma = 1, independent of its opacity (conservative, only larger).
+    const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, 2.f * (kLn255 - log1pf(en)));
+    const float ex = sqrtf(qc * sxx), ey = sqrtf(qc * syy);
+    return splat_rect(f, P.m4.x, P.m4.z, P.m4.y, P.m4.w, ex, ey, P);
 }
 
 // SH records staged in shared memory are padded to 52 floats so per-lane

@@ -72,7 +72,8 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
         float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
     pdl_wait();
     pdl_trigger();
-    blend_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, mean2d, conic, opacity, rgb, image, t_final, n_contrib);
+    const FloatSplats sp{mean2d, conic, opacity, rgb};
+    blend_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, sp, image, t_final, n_contrib);
 }
 
 }  // namespace

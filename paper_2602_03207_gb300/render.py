@@ -52,7 +52,7 @@ class Renderer:
     """Buffers and calls for frames of a fixed (n, width, height, tile)."""
 
     def __init__(self, n, width, height, tile=16, digit_bits=8, key_capacity=None, dilation=0.3,
-                 guard=1.3, flags=0, device="cuda", sort="segmented"):
+                 guard=1.3, flags=0, device="cuda", sort="segmented", packed=False):
         self.n, self.width, self.height = int(n), int(width), int(height)
         self.cfg = capi.config(tile=tile, digit_bits=digit_bits, dilation=dilation, guard=guard,
                                flags=config_flags(flags, sort))
@@ -80,6 +80,12 @@ class Renderer:
         self.image = torch.empty((height, width, 3), dtype=torch.float32, device=d)
         self.t_final = torch.empty((height, width), dtype=torch.float32, device=d)
         self.n_contrib = torch.empty((height, width), dtype=torch.int32, device=d)
+        # packed-record variant (ws_preprocess_packed / ws_rasterize_packed)
+        self.packed = bool(packed)
+        if self.packed:
+            self.mean2d_p = torch.empty((n1, 2), dtype=torch.float32, device=d)
+            self.axes = torch.empty((n1, 2), dtype=torch.int32, device=d)      # 2 x (2 binary16)
+            self.rgba = torch.empty(n1, dtype=torch.int32, device=d)           # RGBA8
         self._cam_probe = None
         self.workspace = None
         self.sorted_in_alt = False
@@ -93,6 +99,11 @@ class Renderer:
 
     # ------------------------------------------------------------ stages
     def preprocess(self, scene, cam, stream=None):
+        if self.packed:
+            capi.ws_preprocess_packed(self.n, scene["means"], scene["log_scales"], scene["quats"],
+                                      scene["opacity_logits"], scene["sh"], cam, self.cfg, self.mean2d_p,
+                                      self.axes, self.rgba, self.depth, self.rect, self.tiles_touched, stream)
+            return
         capi.ws_preprocess(self.n, scene["means"], scene["log_scales"], scene["quats"],
                            scene["opacity_logits"], scene["sh"], cam, self.cfg, self.mean2d, self.conic,
                            self.depth, self.rgb, self.opacity, self.rect, self.tiles_touched, stream)
@@ -116,6 +127,11 @@ class Renderer:
         return self.vals_alt if self.sorted_in_alt else self.vals
 
     def rasterize(self, cam, stream=None):
+        if self.packed:
+            capi.ws_rasterize_packed(self.num_keys, self.sorted_keys, self.sorted_vals, self.mean2d_p, self.axes,
+                                     self.rgba, cam, self.cfg, self.ranges, self.image, self.t_final,
+                                     self.n_contrib, stream)
+            return
         capi.ws_rasterize(self.num_keys, self.sorted_keys, self.sorted_vals, self.mean2d, self.conic,
                           self.opacity, self.rgb, cam, self.cfg, self.ranges, self.image, self.t_final,
                           self.n_contrib, stream)
@@ -135,6 +151,8 @@ class Renderer:
         """Gradients of a loss w.r.t. the Gaussians for the frame last
         rendered by forward() with the same scene and camera; d_image is
         dL/dimage (H, W, 3). Returns a dict of gradient tensors."""
+        if self.packed:
+            raise ValueError("the packed-record variant renders only (no backward)")
         cam = capi.camera(cam_dict)
         d = self.image.device
         n1 = max(self.n, 1)

@@ -397,3 +397,90 @@ def test_ablations_leave_the_image_unchanged():
         ok = (base["n_amb"] == 0) & (out["n_amb"] == 0)
         np.testing.assert_allclose(out["image"][ok], base["image"][ok], atol=1e-14)
         assert out["keys"].size > base["keys"].size
+
+
+# ------------------------------------------------------------ packed record
+
+def test_f16_rounding_is_ieee_binary16():
+    """§3.2 packs the ellipse axes as binary16: or_round_f16 is numpy's
+    float64 -> float16 conversion (round to nearest, ties to even), across
+    the normal and subnormal ranges, exact ties and overflow."""
+    rng = np.random.default_rng(8)
+    x = np.concatenate([
+        rng.uniform(-3, 3, 2000), np.exp(rng.uniform(-20, 11, 2000)) * rng.choice([-1, 1], 2000),
+        # exact ties: odd multiples of half an ulp
+        (2 * rng.integers(1, 1000, 200) + 1) * 2.0 ** -11 + 1.0, 2049.0 + 2 * np.arange(50),
+        (2 * rng.integers(0, 500, 50) + 1) * 2.0 ** -25,   # subnormal ties
+        [0.0, -0.0, 65504.0, 65519.99, 65520.0, 1e6, 5.96e-8, 2.9e-8, 3.0e-8]])
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float16).astype(np.float64)
+    np.testing.assert_array_equal(oracle.round_f16(x), want)
+
+
+def test_axes_reconstruct_the_covariance():
+    """v1 v1^T + v2 v2^T = Sigma', v1 is along the larger eigenvalue and
+    v2 is v1 turned by +90 degrees, with lengths sqrt(l1) >= sqrt(l2) (the
+    eigenvalues numpy's eigh gives), for isotropic, axis-aligned, rotated
+    and very elongated covariances."""
+    rng = np.random.default_rng(9)
+    cases = [(1.0, 0.0, 1.0), (4.0, 0.0, 1.0), (1.0, 0.0, 4.0), (2.0, 1.999, 2.0), (0.3, -0.0, 0.3)]
+    for _ in range(300):
+        l1, l2 = np.sort(np.exp(rng.uniform(-2, 9, 2)))[::-1]
+        th = rng.uniform(0, np.pi)
+        U = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        Sg = U @ np.diag([l1, l2]) @ U.T
+        cases.append((Sg[0, 0], Sg[0, 1], Sg[1, 1]))
+    for sxx, sxy, syy in cases:
+        v1, v2 = oracle.axes(sxx, sxy, syy)
+        Sg = np.array([[sxx, sxy], [sxy, syy]])
+        rec = np.outer(v1, v1) + np.outer(v2, v2)
+        np.testing.assert_allclose(rec, Sg, rtol=1e-12, atol=1e-12 * np.abs(Sg).max())
+        ev = np.linalg.eigvalsh(Sg)
+        np.testing.assert_allclose([v1 @ v1, v2 @ v2], ev[::-1], rtol=1e-10, atol=1e-12 * ev.max())
+        assert abs(v1 @ v2) <= 1e-12 * (v1 @ v1)
+        assert v1[0] * v2[1] - v1[1] * v2[0] >= 0  # v2 is v1 turned by +90 degrees
+
+
+def test_packed_record_quantisation():
+    """With PACKED the pre-processing stores opacity and clamped colour on
+    8 bits (multiples of 1/255 within half a step of the float values), the
+    centre in float32 and the conic of the binary16 axes."""
+    scene = S.uniform_scene(800, seed=61)
+    cam = S.look_at_camera((2.2, -1.0, 0.8), (0.4, 0.0, 0.0), 96, 72)
+    full = oracle.preprocess(scene, cam)
+    pk = oracle.preprocess(scene, cam, flags=oracle.PACKED)
+    vis = pk["touched"] > 0
+    assert vis.sum() > 300
+    for k in ("opacity", "rgb"):
+        q = pk[k][vis] * 255.0
+        np.testing.assert_allclose(q, np.round(q), atol=1e-9)
+        ref = np.clip(full[k][vis], 0.0, 1.0)
+        assert np.abs(pk[k][vis] - ref).max() <= 0.5 / 255 + 1e-12
+    np.testing.assert_array_equal(pk["mean2d"][vis], full["mean2d"][vis].astype(np.float32).astype(np.float64))
+    for i in np.nonzero(vis)[0][:200]:
+        c = full["cov2d"][i]
+        v1, v2 = oracle.axes(c[0], c[1], c[2])
+        v1, v2 = oracle.round_f16(v1), oracle.round_f16(v2)
+        Sg = np.outer(v1, v1) + np.outer(v2, v2)
+        np.testing.assert_allclose(pk["cov2d"][i], [Sg[0, 0], Sg[0, 1], Sg[1, 1]], rtol=1e-15, atol=0)
+        Q = np.linalg.inv(Sg)
+        np.testing.assert_allclose(pk["conic"][i], [Q[0, 0], Q[0, 1], Q[1, 1]], rtol=1e-12)
+        # binary16 axes keep the covariance within ~1e-3 relative
+        assert np.abs(Sg - np.array([[c[0], c[1]], [c[1], c[2]]])).max() <= 2e-3 * max(c[0], c[2])
+
+
+def test_packed_image_close_to_the_float_image():
+    """Where no colour exceeds 1 (nothing for the 8-bit clamp to cut), the
+    packed record changes each pixel by well under 1/255: the quantisation
+    steps are below 1/510 each and alpha-weighted."""
+    scene = S.uniform_scene(1500, seed=62)
+    scene["sh"][:, 0, :] = np.clip(scene["sh"][:, 0, :], -0.6, 0.6)
+    scene["sh"][:, 1:, :] *= 0.2
+    cam = S.look_at_camera((2.2, -1.0, 0.8), (0.4, 0.0, 0.0), 96, 72)
+    full = oracle.render(scene, cam)
+    assert full["proj"]["rgb"][full["proj"]["touched"] > 0].max() < 1.0
+    pk = oracle.render(scene, cam, flags=oracle.PACKED)
+    ok = (full["n_amb"] == 0) & (pk["n_amb"] == 0)
+    d = np.abs(pk["image"] - full["image"])[ok]
+    assert d.max() <= 1.0 / 255, d.max()
+    assert np.median(d) <= 1e-3
