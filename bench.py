@@ -345,6 +345,41 @@ def packed_variant(scene, cams, tile, digit_bits, key_capacity, dev, steps=1000)
             "record_bytes_per_splat": {"packed": 20, "float": 44}}
 
 
+def paper_design(scene, cams, tile, digit_bits, dev, steps=500):
+    """The paper's own design in CUDA (ws_render_quads after ws_preprocess:
+    global 32-bit depth sort in four 8-bit passes, opacity-sized quads,
+    back-to-front "over") on the same frames, timed like the headline."""
+    import torch
+    from paper_2602_03207_gb300 import render
+    n = scene["means"].shape[0]
+    W, H = cams[0]["width"], cams[0]["height"]
+    r = render.Renderer(n, W, H, tile=tile, digit_bits=digit_bits, key_capacity=min((1 << 31) - 1, 6 * n),
+                        device=dev)
+    pairs = 0
+    for cam in cams:
+        r.forward_quads(scene, cam)
+        torch.cuda.synchronize()
+        r.check_quads_status()
+        pairs += r.key_count()
+    for i in range(5):
+        r.forward_quads(scene, cams[i % len(cams)])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(steps):
+        r.forward_quads(scene, cams[i % len(cams)])
+    b.record()
+    torch.cuda.synchronize()
+    r.check_quads_status()
+    ms = a.elapsed_time(b) / steps
+    del r
+    torch.cuda.empty_cache()
+    return {"value": round(1e3 / ms, 2), "unit": "frames/s", "ms_per_step": round(ms, 4), "steps": steps,
+            "mean_pairs_per_frame": int(pairs / len(cams)),
+            "design": "global 32-bit depth sort (4 x 8-bit passes) + quads binned to tiles in depth order + "
+                      "back-to-front over"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -554,6 +589,8 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
         "clocks": clocks,
     }
     out["sort_only"] = sort_only(r.image.device, digit_bits=args.digit_bits)
+    out["paper_design"] = paper_design(scene, cams, r.tile, args.digit_bits, r.image.device,
+                                       steps=min(args.steps, 500))
     out["packed_variant"] = packed_variant(scene, cams, r.tile, args.digit_bits, r.key_capacity, r.image.device,
                                            steps=min(args.steps, 1000))
     if not args.no_ablation:

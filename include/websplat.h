@@ -271,6 +271,32 @@ ws_status ws_rasterize_packed(const uint32_t *num_keys, const uint64_t *keys, co
                               const ws_camera *cam, const ws_config *cfg, uint32_t *ranges, float *image,
                               float *t_final, uint32_t *n_contrib, void *stream);
 
+/* The paper's own render design (§3.3 sort stage, §3.4 rasterisation stage)
+ * in CUDA, for comparison with the tile path: the visible splats
+ * (tiles_touched > 0) are compacted and sorted by their 32-bit float depth
+ * with four stable 8-bit passes; each becomes one quad sized by its opacity
+ * (E8: r = sqrt(ln(255 sigma)) along its ellipse axes) carrying the local
+ * coordinate p of E9 (p . p = q / 2); the quads are binned to screen tiles in
+ * depth order (a stable partition keeps that order per tile) and every tile
+ * composites its quads back to front with "over", C = a c + (1 - a) C, from
+ * the background. A fragment is a pixel centre with |p_x|, |p_y| <= r;
+ * a = min(0.99, sigma e^{-p.p}) and fragments with a < 1/255 are skipped, so
+ * the image equals ws_rasterize's within float rounding.
+ * Inputs (device): the ws_preprocess outputs (mean2d, conic, opacity, rgb,
+ * depth, tiles_touched). keys / vals / keys_alt / vals_alt (device,
+ * key_capacity entries) hold the (tile, rank) pairs of the binning;
+ * num_keys[0] (device) receives their count (WS_FLAG_CAPACITY in the
+ * workspace status word when it exceeds key_capacity). Outputs (device):
+ * image[H][W][3], t_final[H][W]. workspace: ws_quads_workspace_bytes(n,
+ * key_capacity, cam, cfg) bytes, 16-byte aligned; status read with
+ * ws_read_status. Errors as ws_rasterize. */
+size_t ws_quads_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera *cam, const ws_config *cfg);
+ws_status ws_render_quads(int64_t n, const float *mean2d, const float *conic, const float *opacity,
+                          const float *rgb, const float *depth, const uint32_t *tiles_touched, const ws_camera *cam,
+                          const ws_config *cfg, int64_t key_capacity, uint64_t *keys, uint32_t *vals,
+                          uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *num_keys, float *image, float *t_final,
+                          void *workspace, void *stream);
+
 /* Backward of the whole frame for a loss L(image): given d_image = dL/dimage
  * (device, [H][W][3]), writes dL/d(means, log_scales, quats, opacity_logits,
  * sh) (device, the input layouts; zero for culled Gaussians). The paper has

@@ -89,6 +89,9 @@ def lib():
             L.ws_sort.argtypes = [P, I64, I32, I32, P, P, P, P, cfg_p, P, C.POINTER(I32), P]
             L.ws_rasterize.argtypes = [P, P, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
             L.ws_preprocess_packed.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P]
+            L.ws_quads_workspace_bytes.argtypes = [I64, I64, cam_p, cfg_p]
+            L.ws_quads_workspace_bytes.restype = C.c_size_t
+            L.ws_render_quads.argtypes = [I64, P, P, P, P, P, P, cam_p, cfg_p, I64, P, P, P, P, P, P, P, P, P]
             L.ws_rasterize_packed.argtypes = [P, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
             L.ws_rasterize_backward.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P, P, P,
                                                 P, P, P, I64, P, P, P, P, P, P, P]
@@ -212,6 +215,18 @@ def ws_rasterize_packed(num_keys, keys, vals, mean2d, axes, rgba, cam, cfg, rang
     _check("ws_rasterize_packed", lib().ws_rasterize_packed(
         _ptr(num_keys), _ptr(keys), _ptr(vals), _ptr(mean2d), _ptr(axes), _ptr(rgba), C.byref(cam),
         C.byref(cfg), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib), _stream(stream)))
+
+
+def ws_quads_workspace_bytes(n, key_capacity, cam, cfg):
+    return int(lib().ws_quads_workspace_bytes(int(n), int(key_capacity), C.byref(cam), C.byref(cfg)))
+
+
+def ws_render_quads(n, mean2d, conic, opacity, rgb, depth, tiles_touched, cam, cfg, key_capacity, keys, vals,
+                    keys_alt, vals_alt, num_keys, image, t_final, workspace, stream=None):
+    _check("ws_render_quads", lib().ws_render_quads(
+        int(n), _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb), _ptr(depth), _ptr(tiles_touched),
+        C.byref(cam), C.byref(cfg), int(key_capacity), _ptr(keys), _ptr(vals), _ptr(keys_alt), _ptr(vals_alt),
+        _ptr(num_keys), _ptr(image), _ptr(t_final), _ptr(workspace), _stream(stream)))
 
 
 def ws_rasterize_backward(n, means, log_scales, quats, opacity_logits, sh, cam, cfg, mean2d, conic, rgb,

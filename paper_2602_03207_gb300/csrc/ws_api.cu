@@ -301,6 +301,41 @@ ws_status ws_rasterize_packed(const uint32_t* num_keys, const uint64_t* keys, co
                                                    t_final, n_contrib, static_cast<cudaStream_t>(stream)));
 }
 
+size_t ws_quads_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera* cam, const ws_config* cfg) {
+    if (n < 0 || n >= (int64_t(1) << 31) || key_capacity < 0 || key_capacity >= (int64_t(1) << 31)) return 0;
+    if (!valid_camera(cam) || !valid_config(cfg)) return 0;
+    const Frame f = make_frame(cam, cfg);
+    return ws::quad_layout(n, key_capacity, (int64_t)f.TX * f.TY).total;
+}
+
+ws_status ws_render_quads(int64_t n, const float* mean2d, const float* conic, const float* opacity,
+                          const float* rgb, const float* depth, const uint32_t* tiles_touched, const ws_camera* cam,
+                          const ws_config* cfg, int64_t key_capacity, uint64_t* keys, uint32_t* vals,
+                          uint64_t* keys_alt, uint32_t* vals_alt, uint32_t* num_keys, float* image, float* t_final,
+                          void* workspace, void* stream) {
+    if (n < 0 || n >= (int64_t(1) << 31) || key_capacity < 0 || key_capacity >= (int64_t(1) << 31))
+        return WS_ERR_INVALID_ARG;
+    if (!valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, image, t_final, workspace};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (n > 0) {
+        const void* in[] = {mean2d, conic, opacity, rgb, depth, tiles_touched};
+        for (const void* p : in)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    if (key_capacity > 0) {
+        const void* kp[] = {keys, vals, keys_alt, vals_alt};
+        for (const void* p : kp)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    const Frame f = make_frame(cam, cfg);
+    if (f.TX > 65535 || f.TY > 65535) return WS_ERR_UNSUPPORTED;
+    return cuda_status(ws::launch_render_quads(n, mean2d, conic, opacity, rgb, depth, tiles_touched, f, key_capacity,
+                                               keys, vals, keys_alt, vals_alt, num_keys, image, t_final, workspace,
+                                               static_cast<cudaStream_t>(stream)));
+}
+
 ws_status ws_rasterize_backward(int64_t n, const float* means, const float* log_scales,
                                 const float* quats, const float* opacity_logits, const float* sh,
                                 const ws_camera* cam, const ws_config* cfg, const float* mean2d,

@@ -74,6 +74,17 @@ cudaError_t launch_rasterize_packed(const uint32_t* num_keys, const uint64_t* ke
                                     uint32_t* ranges, float* image, float* t_final, uint32_t* n_contrib,
                                     cudaStream_t stream);
 
+// ---- the paper's quad design (global depth sort + back-to-front quads)
+struct QuadLayout {
+    size_t sort, cull, dkeys, dkeys_alt, dvals, dvals_alt, offsets, quad, one, rect, zdepth, num_vis, ranges, total;
+};
+QuadLayout quad_layout(int64_t n, int64_t key_capacity, int64_t ntiles);
+cudaError_t launch_render_quads(int64_t n, const float* mean2d, const float* conic, const float* opacity,
+                                const float* rgb, const float* depth, const uint32_t* tiles_touched,
+                                const Frame& f, int64_t key_capacity, uint64_t* keys, uint32_t* vals,
+                                uint64_t* keys_alt, uint32_t* vals_alt, uint32_t* num_keys, float* image,
+                                float* t_final, void* workspace, cudaStream_t stream);
+
 // ---- backward
 size_t backward_scratch_bytes(int64_t key_capacity);
 cudaError_t launch_backward(int64_t n, const float* means, const float* log_scales, const float* quats,

@@ -147,6 +147,31 @@ class Renderer:
         self.rasterize(cam, stream)
         return self.image
 
+    def forward_quads(self, scene, cam_dict, stream=None):
+        """One frame through the paper's own design (ws_render_quads: global
+        depth sort, opacity-sized quads, back-to-front "over"); image and
+        t_final as forward(). Asynchronous."""
+        if self.packed:
+            raise ValueError("the quad path takes the float pre-processing outputs")
+        cam = capi.camera(cam_dict)
+        self.preprocess(scene, cam, stream)
+        if getattr(self, "quad_workspace", None) is None:
+            nbytes = capi.ws_quads_workspace_bytes(self.n, self.key_capacity, cam, self.cfg)
+            if nbytes == 0:
+                raise ValueError("ws_quads_workspace_bytes rejected the configuration")
+            self.quad_workspace = torch.zeros(nbytes, dtype=torch.uint8, device=self.image.device)
+        capi.ws_render_quads(self.n, self.mean2d, self.conic, self.opacity, self.rgb, self.depth,
+                             self.tiles_touched, cam, self.cfg, self.key_capacity, self.keys, self.vals,
+                             self.keys_alt, self.vals_alt, self.num_keys, self.image, self.t_final,
+                             self.quad_workspace, stream)
+        return self.image
+
+    def check_quads_status(self, stream=None):
+        flags = capi.ws_read_status(self.quad_workspace, clear=False, stream=stream)
+        if flags & capi.WS_FLAG_CAPACITY:
+            raise capi.WsError("quads", capi.WS_ERR_CAPACITY)
+        return flags
+
     def backward(self, scene, cam_dict, d_image, stream=None):
         """Gradients of a loss w.r.t. the Gaussians for the frame last
         rendered by forward() with the same scene and camera; d_image is
