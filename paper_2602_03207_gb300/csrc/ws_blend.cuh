@@ -322,17 +322,35 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
                     }
                 }
                 if (__any_sync(kFull, any)) {
+                    // Warp sums of the 9 partials in a fixed order with 14
+                    // shuffles: partials 0..7 by reduce-scatter (each step
+                    // hands half of a lane's values to its partner, so after
+                    // offsets 16, 8, 4 lane l holds partial (l >> 2) & 7
+                    // summed over 8 lanes, then two butterfly steps finish
+                    // it), partial 8 by a butterfly.
+                    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+                    float h4[4];
 #pragma unroll
-                    for (int c = 0; c < kPart; ++c) {
-                        float v = acc[c];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-                        acc[c] = v;
+                    for (int q = 0; q < 4; ++q) {
+                        const float give = b4 ? acc[q] : acc[4 + q];
+                        const float keep = b4 ? acc[4 + q] : acc[q];
+                        h4[q] = keep + __shfl_xor_sync(kFull, give, 16);
                     }
-                    if (lane == 0) {
+                    float h2[2];
 #pragma unroll
-                        for (int c = 0; c < kPart; ++c) s_part[j][warp][c] = acc[c];
+                    for (int q = 0; q < 2; ++q) {
+                        const float give = b3 ? h4[q] : h4[2 + q];
+                        const float keep = b3 ? h4[2 + q] : h4[q];
+                        h2[q] = keep + __shfl_xor_sync(kFull, give, 8);
                     }
+                    float h1 = (b2 ? h2[1] : h2[0]) + __shfl_xor_sync(kFull, b2 ? h2[0] : h2[1], 4);
+                    h1 += __shfl_xor_sync(kFull, h1, 2);
+                    h1 += __shfl_xor_sync(kFull, h1, 1);
+                    float v8 = acc[8];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(kFull, v8, o);
+                    if ((lane & 3) == 0) s_part[j][warp][lane >> 2] = h1;
+                    if (lane == 0) s_part[j][warp][8] = v8;
                 }
             }
         }
