@@ -467,11 +467,9 @@ def run_ours(args):
         e[4].record(stream)
     torch.cuda.synchronize()
     r.check_status()
-    stage_ms = {s: 0.0 for s in STAGES}
-    for e in ev:
-        for j, s in enumerate(STAGES):
-            stage_ms[s] += e[j].elapsed_time(e[j + 1])
-    stage_ms = {s: v / stage_steps for s, v in stage_ms.items()}
+    per = {s: [e[j].elapsed_time(e[j + 1]) for e in ev] for j, s in enumerate(STAGES)}
+    stage_ms = {s: sum(v) / stage_steps for s, v in per.items()}
+    stage_p99 = {s: float(np.percentile(v, 99)) for s, v in per.items()}
 
     # end to end through the public API: pinned host scene in, image out
     e2e = None
@@ -507,6 +505,7 @@ def run_ours(args):
     if rank == 0:
         result = summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clk.summary(),
                            launches_per_frame * args.steps, passes, world)
+        result["stages_p99_ms"] = {k: round(v, 4) for k, v in stage_p99.items()}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -559,9 +558,14 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     peak_tflops = sm_count * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
     ach = flops / (ms * 1e-3) / 1e12
+    # the SFU side: one ex2 per evaluation against 16 SFU results per clock per SM
+    sfu_peak = sm_count * 16 * peaks["sm_max_mhz"] * 1e6
+    sfu_rate = evals / (ms * 1e-3)
     stages["rasterize"] = {"ms": round(ms, 4), "bound": "alu", "alg_evals": int(evals),
                            "achieved_tflops": round(ach, 3), "peak_tflops": round(peak_tflops, 2),
-                           "frac": round(ach / peak_tflops, 4)}
+                           "frac": round(ach / peak_tflops, 4),
+                           "sfu": {"achieved_gex2_s": round(sfu_rate / 1e9, 1),
+                                   "peak_gex2_s": round(sfu_peak / 1e9, 1), "frac": round(sfu_rate / sfu_peak, 4)}}
     # The dominant single kernel of a frame is k_blend (largest share of the
     # ncu launch list). Its timed span is the ws_rasterize call, which also
     # holds the two small tile-range kernels, so the fraction is conservative.
