@@ -38,7 +38,7 @@
  *                       gradient w.r.t. every input (the paper renders only;
  *                       §1 notes 3DGS is differentiable).
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   - parameterisation: s = exp(log_scale), q = (w,x,y,z) normalised,
  *     sigma = 1 / (1 + exp(-logit)); Sigma = R diag(s^2) R^T.
  *   - projection: pinhole with OpenCV axes, pixel u spans [u, u+1) and its
