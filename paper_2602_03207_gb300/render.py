@@ -209,6 +209,58 @@ class Renderer:
         return int(self.offsets[self.n].item()) & 0xFFFFFFFF
 
 
+class FramePipeline:
+    """Frames whose scene and image live in host memory: every frame uploads
+    its scene from (pinned) host memory and reads its image back. Each of
+    `slots` slots owns a Renderer, a device copy of the scene and a stream;
+    uploads run in frame order on one upload stream, so frame i+1's upload
+    overlaps frame i's render and read-back and a stream of frames runs at
+    the pace of the host-device link rather than upload + render + read-back
+    in series. A slot is reused only after its previous frame's read-back has
+    finished. Everything is asynchronous; synchronize() waits for all frames
+    and checks each renderer's status."""
+
+    def __init__(self, n, width, height, slots=2, device="cuda", **renderer_kw):
+        self.device = torch.device(device)
+        self.slots = []
+        for _ in range(int(slots)):
+            self.slots.append({"r": Renderer(n, width, height, device=self.device, **renderer_kw),
+                               "scene": None, "stream": torch.cuda.Stream(self.device), "done": None})
+        self.upload = torch.cuda.Stream(self.device)
+        self.count = 0
+
+    def streams(self):
+        return [self.upload] + [s["stream"] for s in self.slots]
+
+    def submit(self, host_scene, cam_dict, host_image):
+        """Queue one frame: upload host_scene (dict of CPU tensors, ideally
+        pinned), render with cam_dict, copy the image into host_image (a CPU
+        float32 tensor of shape (H, W, 3), ideally pinned). Returns at once."""
+        s = self.slots[self.count % len(self.slots)]
+        self.count += 1
+        if s["scene"] is None:
+            s["scene"] = {k: torch.empty(tuple(host_scene[k].shape), dtype=torch.float32, device=self.device)
+                          for k in SCENE_KEYS}
+        if s["done"] is not None:
+            self.upload.wait_event(s["done"])
+        with torch.cuda.stream(self.upload):
+            for k in SCENE_KEYS:
+                s["scene"][k].copy_(host_scene[k], non_blocking=True)
+            up = torch.cuda.Event()
+            up.record(self.upload)
+        s["stream"].wait_event(up)
+        with torch.cuda.stream(s["stream"]):
+            s["r"].forward(s["scene"], cam_dict)
+            host_image.copy_(s["r"].image, non_blocking=True)
+            s["done"] = torch.cuda.Event()
+            s["done"].record(s["stream"])
+
+    def synchronize(self):
+        torch.cuda.synchronize(self.device)
+        for s in self.slots:
+            s["r"].check_status()
+
+
 def render(scene, cam_dict, tile=16, digit_bits=8, key_capacity=None, flags=0, sort="segmented"):
     """Render one frame of a device scene dict; returns (image, renderer).
 

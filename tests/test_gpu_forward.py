@@ -294,3 +294,24 @@ def test_ply_scene_renders_like_the_original(tmp_path):
     np.testing.assert_array_equal(a["image"], b["image"])
     st = compare_image(a, oracle.render(loaded, cam))
     assert st["n_bad"] == 0, st
+
+
+def test_frame_pipeline_matches_renderer():
+    """Frames from host memory through render.FramePipeline (uploads
+    overlapping renders on two slots) are bit-identical to Renderer frames."""
+    import torch
+    from paper_2602_03207_gb300 import render
+    scene, _ = S.small_forward()
+    cams = [S.look_at_camera((2.2 * np.cos(a), 2.2 * np.sin(a), 0.8), (0.0, 0.0, 0.0), 200, 150)
+            for a in np.linspace(0, 2, 5)]
+    host = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).pin_memory() for k in render.SCENE_KEYS}
+    outs = [torch.empty((150, 200, 3), dtype=torch.float32).pin_memory() for _ in cams]
+    pipe = render.FramePipeline(scene["means"].shape[0], 200, 150, key_capacity=200_000)
+    for c, o in zip(cams, outs):
+        pipe.submit(host, c, o)
+    pipe.synchronize()
+    dev = render.scene_to_device(scene)
+    r = render.Renderer(scene["means"].shape[0], 200, 150, key_capacity=200_000)
+    for c, o in zip(cams, outs):
+        ref = r.forward(dev, c).cpu()
+        np.testing.assert_array_equal(o.numpy(), ref.numpy())
