@@ -306,7 +306,7 @@ ws_status ws_render_quads(int64_t n, const float *mean2d, const float *conic, co
  * channel clamped at 0.
  * Deterministic, without float atomics: each tile walks its list back to
  * front from t_final / n_contrib, reduces each pair's 9 partial derivatives
- * (centre 2, conic 3, sigma 1, colour 3) inside the block in a fixed order
+ * (centre 2, conic 3, sigma 1 (times sigma), colour 3) inside the block in a fixed order
  * and writes them to the pair's emission slot offsets[g] + k in the
  * workspace; each Gaussian then sums its slots in order and applies the
  * adjoint of its pre-processing. Bitwise reproducible.

@@ -12,8 +12,11 @@
 //   background and is updated B <- a c + (1 - a) B):
 //     dL/dc_i = a_i T_i dL/dC,   dL/da_i = T_i (c_i - B_i) . dL/dC,
 //   then, unless the alpha was clamped at 0.99,
-//     dL/dsigma = G dL/da, dL/dpower = a dL/da, power = -1/2 d^T Q d,
+//     sigma dL/dsigma = raw dL/da (raw = sigma G, the unclamped alpha),
+//     dL/dpower = a dL/da, power = -1/2 d^T Q d,
 //   giving d/dmean = Q d, d/dQ_a = -dx^2/2, d/dQ_b = -dx dy, d/dQ_c = -dy^2/2.
+//   (The sigma partial is kept multiplied by sigma: dL/dlogit is then that
+//   sum times 1 - sigma.)
 //   Each warp reduces its 32 pixels with a fixed shuffle tree, the block
 //   adds its warps in warp order, and the record goes to the pair's slot.
 // k_preprocess_bwd: one thread per Gaussian: slot-ordered sum of its
@@ -79,7 +82,7 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
         X[1] = __ldg(means + 3 * i + 1);
         X[2] = __ldg(means + 3 * i + 2);
         const float sig = __ldg(opacity + i);
-        glogit = pr[5] * sig * (1.f - sig);
+        glogit = pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
 
         const float4 q4 = __ldg(quats + i);
         const float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1), __ldg(log_scales + 3 * i + 2)};

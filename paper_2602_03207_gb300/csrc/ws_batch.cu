@@ -197,7 +197,7 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
         for (uint32_t s = 0; s < cnt; ++s)
 #pragma unroll
             for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
-        glogit += pr[5] * sig * (1.f - sig);
+        glogit += pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
         const Frame& f = ft.f[v];
         splat_adjoint(f, X, q4, ls, pr, gm, gls, gq);
         const float col[3] = {__ldg(rgb + 3 * o), __ldg(rgb + 3 * o + 1), __ldg(rgb + 3 * o + 2)};

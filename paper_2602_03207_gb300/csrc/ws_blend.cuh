@@ -151,7 +151,7 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
 
 
 constexpr int kBwdBatch = 64;
-constexpr int kPart = 9;  // dmean x, y; dconic a, b, c; dsigma; drgb r, g, b
+constexpr int kPart = 9;  // dmean x, y; dconic a, b, c; sigma dsigma; drgb r, g, b
 
 struct BwdRec {
     float4 geo;   // tile-relative centre x, y; premultiplied conic A, B
@@ -295,8 +295,6 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
                     if (!(e >= kLog2AlphaMin)) continue;
                     const float raw = ex2_approx(e);
                     const float alpha = fminf(kAlphaMax, raw);
-                    // d alpha / d sigma = exp(-q/2) = 2^(e - log2 sigma)
-                    const float G = ex2_approx(e - r.geo2.y);
                     any = true;
                     const float Tb = T[k] / (1.f - alpha);
                     const float w = alpha * Tb;
@@ -311,7 +309,9 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
                     dalpha *= Tb;
                     T[k] = Tb;
                     if (raw < kAlphaMax) {
-                        acc[5] = fmaf(G, dalpha, acc[5]);
+                        // partial 5 is sigma dL/dsigma = raw dL/dalpha
+                        // (d alpha / d sigma = exp(-q/2) = raw / sigma)
+                        acc[5] = fmaf(raw, dalpha, acc[5]);
                         const float dp = alpha * dalpha;
                         const float ca = r.geo2.z, cb = r.geo2.w, cc2 = r.col.w;
                         acc[0] = fmaf(dp, ca * dx + cb * dy, acc[0]);

@@ -118,3 +118,17 @@ def test_packed_close_to_float_path_and_deterministic():
     np.testing.assert_array_equal(a["image"], b["image"])
     f = fetch(gpu_frame(scene, cam, key_capacity=40 * 3000))
     assert np.abs(a["image"] - f["image"]).max() <= 1.0 / 255
+
+
+def test_packed_empty_and_fully_culled():
+    """n = 0 and a scene whose every splat is below 1/255 both give the
+    background with transmittance 1."""
+    cam = S.look_at_camera((2.2, -1.0, 0.8), (0.4, 0.0, 0.0), 64, 48)
+    empty = {k: v[:0] for k, v in S.uniform_scene(10, seed=1).items()}
+    culled = S.uniform_scene(300, seed=2)
+    culled["opacity_logits"][:] = -9.0
+    for sc in (empty, culled):
+        g = packed_frame(sc, cam, key_capacity=4096)
+        assert g["num_keys"] == 0
+        np.testing.assert_array_equal(g["t_final"], np.ones_like(g["t_final"]))
+        np.testing.assert_allclose(g["image"], np.broadcast_to(np.asarray(cam["bg"], np.float32), g["image"].shape))

@@ -91,3 +91,12 @@ def test_quads_empty_scene():
     g = quad_frame(scene, cam, key_capacity=4096)
     np.testing.assert_array_equal(g["t_final"], np.ones_like(g["t_final"]))
     np.testing.assert_allclose(g["image"], np.broadcast_to(np.asarray(cam["bg"], np.float32), g["image"].shape))
+
+
+def test_quads_no_gaussians():
+    cam = S.look_at_camera((2.2, -1.0, 0.8), (0.4, 0.0, 0.0), 64, 48)
+    empty = {k: v[:0] for k, v in S.uniform_scene(10, seed=1).items()}
+    g = quad_frame(empty, cam, key_capacity=4096)
+    assert g["num_keys"] == 0
+    np.testing.assert_array_equal(g["t_final"], np.ones_like(g["t_final"]))
+    np.testing.assert_allclose(g["image"], np.broadcast_to(np.asarray(cam["bg"], np.float32), g["image"].shape))
