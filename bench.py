@@ -386,6 +386,8 @@ def run_ours(args):
     from paper_2602_03207_gb300 import capi, render
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "train":
+        return run_train(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -626,6 +628,50 @@ def cpu_baseline(args, frames=2):
 
 # ------------------------------------------------------------ batched views
 
+def run_train(args):
+    """Single-view training steps: forward + L2 residual + backward of the
+    500,000-Gaussian 1280x720 scene against a U[0,1) target (the gradient
+    parity workload), CUDA events around the run."""
+    import torch
+    from paper_2602_03207_gb300 import capi, render, synthetic as S
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    scene_np, cam, target = S.grad_scene()
+    n = scene_np["means"].shape[0]
+    scene = render.scene_to_device(scene_np, dev)
+    tgt = torch.as_tensor(target, device=dev)
+    d = torch.empty_like(tgt)
+    r = render.Renderer(n, cam["width"], cam["height"], tile=args.tile, digit_bits=args.digit_bits,
+                        key_capacity=4 * n, device=dev)
+
+    def step():
+        r.forward(scene, cam)
+        capi.ws_image_residual(tgt.numel(), r.image, tgt, d)
+        r.backward(scene, cam, d)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    r.check_status()
+    steps = max(3, min(args.steps, 500))
+    with ClockSampler(dev.index) as clk:
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            step()
+        z.record()
+        torch.cuda.synchronize()
+    t = a.elapsed_time(z) / 1e3 / steps
+    r.check_status()
+    return {"metric": "720p fwd+bwd steps/s at 500k splats", "value": round(1.0 / t, 2), "unit": "steps/s",
+            "n_gpus": 1, "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": round(t * 1e3, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded cluster scene, U[0,1) target)",
+            "config": {"workload": "500,000 Gaussians, 1280x720, SH3, forward + L2 residual + backward",
+                       "tile": args.tile, "pairs": r.key_count()},
+            "clocks": clk.summary()}
+
+
 def run_batch(args):
     """Batched forward + backward of the 2,000,000-Gaussian scene over 64
     seeded views (uneven resolutions 320x240 .. 1920x1080): one training step
@@ -646,7 +692,13 @@ def run_batch(args):
                for c in cams]
     tgt = torch.cat([t.reshape(-1) for t in targets])
     log = (lambda m: print(m, file=sys.stderr, flush=True))
-    best = autotune.tune(scene, cams, tgt, log=log)
+    if args.no_autotune:
+        k = autotune.measure_capacity(scene, cams, args.tile, args.digit_bits)
+        best = {"tile": args.tile, "digit_bits": args.digit_bits,
+                "key_capacity": min((1 << 31) - 1, int(math.ceil(k * 1.1 / 4096) * 4096) + 4096),
+                "table": None, "cached": None}
+    else:
+        best = autotune.tune(scene, cams, tgt, log=log)
     b = batch.BatchRenderer(n, cams, tile=best["tile"], digit_bits=best["digit_bits"],
                             key_capacity=best["key_capacity"], device=dev)
     g = b.capture(scene, tgt)
@@ -666,6 +718,21 @@ def run_batch(args):
     pairs = b.key_count()
     del g
 
+    V = len(cams)
+    out = {
+        "metric": "batched fwd+bwd views/s", "value": round(V / t_batch, 2), "unit": "views/s", "n_gpus": 1,
+        "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": round(t_batch * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded 64-cluster scene, 64 orbit views, random U[0,1) targets)",
+        "config": {"workload": "2,000,000 Gaussians x 64 views 320x240..1920x1080, fwd + L2 residual + bwd",
+                   "tile": best["tile"], "digit_bits": best["digit_bits"], "pairs": pairs,
+                   "autotune": best.get("table"), "autotune_cached": best.get("cached")},
+        "clocks": clk.summary(),
+    }
+    if args.no_plain:
+        return out
+    del b
+    torch.cuda.empty_cache()
     # plain path: one renderer per view, forward + residual + backward per view
     plain = []
     for c, t in zip(cams, targets):
@@ -695,20 +762,12 @@ def run_batch(args):
     z.record()
     torch.cuda.synchronize()
     t_plain = a.elapsed_time(z) / 1e3 / psteps
-    V = len(cams)
-    return {
-        "metric": "batched fwd+bwd views/s", "value": round(V / t_batch, 2), "unit": "views/s", "n_gpus": 1,
-        "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": round(t_batch * 1e3, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded 64-cluster scene, 64 orbit views, random U[0,1) targets)",
-        "config": {"workload": "2,000,000 Gaussians x 64 views 320x240..1920x1080, fwd + L2 residual + bwd",
-                   "tile": best["tile"], "digit_bits": best["digit_bits"], "pairs": pairs,
-                   "autotune": best.get("table"), "autotune_cached": best.get("cached")},
+    out.update({
         "plain": {"value": round(V / t_plain, 2), "unit": "views/s", "ms_per_step": round(t_plain * 1e3, 3),
                   "note": "64 per-view forward + residual + backward calls, per-view gradients not summed"},
         "speedup_vs_plain": round(t_plain / t_batch, 3),
-        "clocks": clk.summary(),
-    }
+    })
+    return out
 
 
 # ------------------------------------------------------------- reference
@@ -721,6 +780,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
+    if args.workload not in WORKLOADS:
+        return {"impl": "reference", "unavailable": f"the oracle arm times the frame workloads "
+                                                      f"({', '.join(sorted(WORKLOADS))}), not '{args.workload}'"}
     import oracle
     oracle.build()
     scene_np, cams = workload(args.workload)
@@ -750,12 +812,14 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hd", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--workload", default="hd", choices=sorted(WORKLOADS) + ["batch", "train"])
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--digit-bits", type=int, default=9)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="batch: use --tile / --digit-bits as given")
+    ap.add_argument("--no-plain", action="store_true", help="batch: skip the per-view comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
