@@ -186,12 +186,13 @@ ws_status ws_sort(const uint32_t *num_keys, int64_t key_capacity, int32_t begin_
  * partitions the pairs by segment with the wait-free passes above, finds
  * every segment's first position, and sorts each segment by its sub-key on
  * chip (a warp per segment of at most 256 keys, a block otherwise). The
- * output, ties included, is bit-identical to the default, with fewer passes
- * over the whole key array (13 tile bits: 2 instead of 5 at 9-bit digits).
+ * partition uses as few passes as digits of at most cfg->digit_bits bits
+ * allow. The output, ties included, is bit-identical to the default, with
+ * fewer passes over the whole key array (13 tile bits: 2 instead of 5 at
+ * 9-bit digits).
  * It applies when 0 <= begin_bit < 31 < end_bit <= 55 and the workspace's
- * sort region holds the 2^(end_bit - 31) + 1 segment starts (at about
- * 1792 segments per 2048 keys of capacity); otherwise ws_sort runs the
- * default sort. Segments of more than 2048 keys are sorted by one block
+ * sort region holds the 2^(end_bit - 31) + 1 segment starts (about one per
+ * key of capacity, at most 2^24 + 1); otherwise ws_sort runs the default sort. Segments of more than 2048 keys are sorted by one block
  * through global memory, correct at any size but slower. */
 
 /* Test hook of the look-back variant: tile `stalled_tile` of the first pass

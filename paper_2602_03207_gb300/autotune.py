@@ -19,7 +19,7 @@ import torch
 from .batch import BatchRenderer
 
 TILES = (8, 16, 32)
-DIGITS = (8, 9, 10)
+DIGITS = (8, 10, 11)
 
 
 def cache_path():

@@ -71,9 +71,9 @@ Layout layout(int64_t n, int64_t cap) {
     Layout L;
     L.status = 0;
     L.sort = align_up(ws::kStatusBytes);
-    const size_t sort_bytes = ws::sort_scratch_bytes(cap, kMaxDigitBits) > ws::sort_lookback_scratch_bytes(cap)
-                                  ? ws::sort_scratch_bytes(cap, kMaxDigitBits)
-                                  : ws::sort_lookback_scratch_bytes(cap);
+    size_t sort_bytes = ws::sort_scratch_bytes(cap, kMaxDigitBits);
+    if (ws::sort_lookback_scratch_bytes(cap) > sort_bytes) sort_bytes = ws::sort_lookback_scratch_bytes(cap);
+    if (ws::sort_segmented_scratch_bytes(cap) > sort_bytes) sort_bytes = ws::sort_segmented_scratch_bytes(cap);
     L.bwd = L.sort + align_up(sort_bytes);
     L.cull = L.bwd + align_up(ws::backward_scratch_bytes(cap));
     L.total = L.cull + align_up(ws::cull_scratch_bytes(n));
@@ -203,7 +203,8 @@ ws_status ws_sort(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_
                                      static_cast<cudaStream_t>(stream));
     } else if ((cfg->flags & WS_CFG_SORT_SEGMENTED) &&
                ws::sort_segmented_supported(key_capacity, begin_bit, end_bit)) {
-        e = ws::launch_sort_segmented(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, vals_alt,
+        e = ws::launch_sort_segmented(num_keys, key_capacity, begin_bit, end_bit, cfg->digit_bits, keys, vals,
+                                      keys_alt, vals_alt,
                                       ws_base + layout(0, key_capacity).sort, &in_alt,
                                       static_cast<cudaStream_t>(stream));
     } else {

@@ -37,9 +37,10 @@ cudaError_t launch_sort(const uint32_t* num_keys, int64_t key_capacity, int begi
 
 // single-sweep (decoupled look-back) variant
 bool sort_segmented_supported(int64_t key_capacity, int begin_bit, int end_bit);
+size_t sort_segmented_scratch_bytes(int64_t key_capacity);
 cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,
-                                  uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                                  void* scratch, int* in_alt, cudaStream_t stream);
+                                  int digit_bits, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                                  uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream);
 bool sort_lookback_supported(int digit_bits, int begin_bit, int end_bit);
 size_t sort_lookback_scratch_bytes(int64_t key_capacity);
 cudaError_t launch_sort_lookback(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,

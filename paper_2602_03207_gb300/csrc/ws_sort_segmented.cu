@@ -463,26 +463,37 @@ k_seg_sort(uint64_t* kin, uint32_t* vin, uint64_t* kout, uint32_t* vout, const u
         warp_sort<8>(kin, vin, kout, vout, b, n, begin_bit, bk, bv, bi);
 }
 
-size_t seg_start_offset_words(int64_t key_capacity) { return sort_scratch_bytes(key_capacity, 8) / 4; }
+// Scratch: [partition histograms, sized for 11-bit digits | segment starts].
+size_t seg_start_offset_words(int64_t key_capacity) { return sort_scratch_bytes(key_capacity, 11) / 4; }
+
+size_t seg_starts_words(int64_t key_capacity) {
+    const size_t w = sort_scratch_bytes(key_capacity, 11) / 4;
+    const size_t most = (size_t(1) << kMaxSegBits) + 1;
+    return w < most ? w : most;
+}
 
 }  // namespace
+
+size_t sort_segmented_scratch_bytes(int64_t key_capacity) {
+    return (seg_start_offset_words(key_capacity) + seg_starts_words(key_capacity)) * sizeof(uint32_t);
+}
 
 bool sort_segmented_supported(int64_t key_capacity, int begin_bit, int end_bit) {
     if (begin_bit < 0 || begin_bit >= kSplitBit || end_bit <= kSplitBit || end_bit - kSplitBit > kMaxSegBits)
         return false;
     const uint64_t nseg = uint64_t(1) << (end_bit - kSplitBit);
-    const size_t words = sort_scratch_bytes(key_capacity, 11) / 4;
-    const size_t used = seg_start_offset_words(key_capacity);
-    return words > used && nseg + 1 <= words - used;
+    return nseg + 1 <= seg_starts_words(key_capacity);
 }
 
 cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,
-                                  uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                                  void* scratch, int* in_alt, cudaStream_t stream) {
-    // Partition by the segment bits: as few passes as 8-bit digits allow,
-    // their width split evenly (13 segment bits: 7 + 6).
+                                  int digit_bits, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                                  uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream) {
+    // Partition by the segment bits: as few passes as digits of at most
+    // digit_bits bits allow, their width split evenly (13 segment bits at
+    // digit_bits 8 or 9: 7 + 6).
     const int seg_bits = end_bit - kSplitBit;
-    const int passes = (seg_bits + 7) / 8;
+    const int max_digit = digit_bits < 4 ? 4 : (digit_bits > 11 ? 11 : digit_bits);
+    const int passes = (seg_bits + max_digit - 1) / max_digit;
     const int digit = (seg_bits + passes - 1) / passes;
     int part_alt = 0;
     cudaError_t e = launch_sort(num_keys, key_capacity, kSplitBit, end_bit, digit < 4 ? 4 : digit, keys, vals,
