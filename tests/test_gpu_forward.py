@@ -315,3 +315,34 @@ def test_frame_pipeline_matches_renderer():
     for c, o in zip(cams, outs):
         ref = r.forward(dev, c).cpu()
         np.testing.assert_array_equal(o.numpy(), ref.numpy())
+
+
+def test_screen_filling_splats():
+    """A few splats whose extent spans most of the screen (hundreds of tiles
+    each: the emission's binary-search path) over many small ones, with two
+    dense clusters so that one tile holds more than 2,048 pairs and another
+    257 to 2,048 (the segmented sort's global-memory and block paths):
+    pre-processing, emission, sort and image against the oracle."""
+    scene = S.uniform_scene(6000, seed=91)
+    rng = np.random.default_rng(92)
+    big = np.arange(12)
+    scene["means"][big] = rng.uniform(-0.5, 0.5, (12, 3))
+    scene["log_scales"][big] = np.log(rng.uniform(0.6, 1.5, (12, 3)))
+    scene["opacity_logits"][big] = -2.0  # sigma ~ 0.12: wide, translucent
+    # two dense clusters of tiny splats: ~3,000 pairs in one tile (the
+    # segmented sort's global-memory path) and ~700 in another (its block path)
+    for sl, centre in ((slice(100, 3100), (0.3, 0.2, 0.1)), (slice(3100, 3800), (-0.4, -0.1, 0.2))):
+        k = sl.stop - sl.start
+        scene["means"][sl] = np.asarray(centre) + rng.normal(0.0, 0.004, (k, 3))
+        scene["log_scales"][sl] = -7.0
+    cam = S.look_at_camera((2.6, -1.0, 0.9), (0.0, 0.0, 0.0), 320, 240)
+    g = fetch(gpu_frame(scene, cam, key_capacity=60 * 6000))
+    ref = oracle.render(scene, cam)
+    assert ref["proj"]["touched"][big].max() >= 200
+    counts = np.sort(ref["ranges"][:, 1] - ref["ranges"][:, 0])[::-1]
+    assert counts[0] > 2048 and 256 < counts[1] <= 2048, counts[:4]
+    _check_preprocess(g, ref)
+    _check_emission(g, ref)
+    _check_sort(g)
+    st = compare_image(g, ref)
+    assert st["n_bad"] == 0, st
