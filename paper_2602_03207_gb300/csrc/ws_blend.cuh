@@ -112,39 +112,24 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
             for (int base = 0; base < cnt; base += 32) {
                 const int jj = base + lane;
                 uint32_t bits = __ballot_sync(kFull, jj < cnt && ((s_mask[jj] >> blk) & 1u));
-                // Two splats per step, composited in list order; both
-                // branch-free: a skipped pair (or a missing second splat)
-                // adds w = 0, which leaves C and T bit for bit unchanged.
+                // Branch-free per splat: a skipped pair adds w = 0, which
+                // leaves C and T bit for bit unchanged.
                 while (bits) {
-                    const int j1 = base + __ffs(bits) - 1;
+                    const int j = base + __ffs(bits) - 1;
                     bits &= bits - 1;
-                    const bool has2 = bits != 0u;
-                    const int j2 = has2 ? base + __ffs(bits) - 1 : j1;
-                    bits &= bits - 1;
-                    const float4 ga = s_rec[j1].geo;
-                    const float2 ha = *reinterpret_cast<const float2*>(&s_rec[j1].geo2);
-                    const float4 gb = s_rec[j2].geo;
-                    const float2 hb = *reinterpret_cast<const float2*>(&s_rec[j2].geo2);
-                    const float ea = splat_log2_alpha(px[k] - ga.x, py[k] - ga.y, ga.z, ga.w, ha.x, ha.y);
-                    const float eb = splat_log2_alpha(px[k] - gb.x, py[k] - gb.y, gb.z, gb.w, hb.x, hb.y);
-                    const bool ka = ea >= kLog2AlphaMin;
-                    const bool kb = has2 && eb >= kLog2AlphaMin;
-                    const float aa = fminf(kAlphaMax, ex2_approx(ea));
-                    const float ab = fminf(kAlphaMax, ex2_approx(eb));
-                    const float4 ca = s_rec[j1].col;
-                    const float wa = ka ? aa * T[k] : 0.f;
-                    C0[k] = fmaf(ca.x, wa, C0[k]);
-                    C1[k] = fmaf(ca.y, wa, C1[k]);
-                    C2[k] = fmaf(ca.z, wa, C2[k]);
-                    T[k] = T[k] - wa;
-                    last[k] = ka ? start + j1 + 1 - range.x : last[k];
-                    const float4 cb = s_rec[j2].col;
-                    const float wb = kb ? ab * T[k] : 0.f;
-                    C0[k] = fmaf(cb.x, wb, C0[k]);
-                    C1[k] = fmaf(cb.y, wb, C1[k]);
-                    C2[k] = fmaf(cb.z, wb, C2[k]);
-                    T[k] = T[k] - wb;
-                    last[k] = kb ? start + j2 + 1 - range.x : last[k];
+                    const float4 geo = s_rec[j].geo;
+                    const float2 geo2 = *reinterpret_cast<const float2*>(&s_rec[j].geo2);
+                    const float dx = px[k] - geo.x, dy = py[k] - geo.y;
+                    const float e = splat_log2_alpha(dx, dy, geo.z, geo.w, geo2.x, geo2.y);
+                    const bool keep = e >= kLog2AlphaMin;
+                    const float alpha = fminf(kAlphaMax, ex2_approx(e));
+                    const float w = keep ? alpha * T[k] : 0.f;
+                    const float4 col = s_rec[j].col;
+                    C0[k] = fmaf(col.x, w, C0[k]);
+                    C1[k] = fmaf(col.y, w, C1[k]);
+                    C2[k] = fmaf(col.z, w, C2[k]);
+                    T[k] = T[k] - w;
+                    last[k] = keep ? start + j + 1 - range.x : last[k];
                 }
             }
         }
