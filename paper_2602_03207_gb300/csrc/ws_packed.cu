@@ -128,10 +128,15 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
         l2 = __ldg(log_scales + 3 * i + 2);
     }
     const bool opaque_enough = valid && passes_opacity(f, logit);
-    const uint32_t need = __ballot_sync(kFull, opaque_enough);
+    const float d = valid ? view_depth(f, x, y, z) : 0.f;
+    // SH records of the lanes that will probably be visible are copied early
+    // (overlapping the projection), the rest of the visible ones afterwards;
+    // the test is the float path's (ws_preprocess.cu).
+    const bool likely = opaque_enough && likely_visible(f, x, y, z, d, l0, l1, l2);
+    const uint32_t need = __ballot_sync(kFull, likely);
     float* stage = s_sh[warp];
+    const float4* src = sh + warp_first * 12;
     if (need) {
-        const float4* src = sh + warp_first * 12;
 #pragma unroll
         for (int r = 0; r < 12; ++r) {
             const int v = lane + r * kWarp;
@@ -146,7 +151,6 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
     uint2 ax = make_uint2(0u, 0u);
     uint32_t a8 = 0;
     if (valid) {
-        const float d = view_depth(f, x, y, z);
         depth[i] = d;
         vis = opaque_enough && d > f.znear;
         float sxx, sxy, syy;
@@ -167,7 +171,17 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
         }
     }
 
-    if (need) {
+    const uint32_t late = __ballot_sync(kFull, vis && !likely);
+    if (late) {
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+            const int v = lane + r * kWarp;
+            const int g = v / 12, c = v - g * 12;
+            if ((late >> g) & 1u) cp_async16(stage + g * kShPad + 4 * c, src + v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    if (need | late) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
         if (vis) {

@@ -48,18 +48,21 @@ k_preprocess(int64_t n, const float* __restrict__ means, const float* __restrict
         l2 = __ldg(log_scales + 3 * i + 2);
     }
     const bool opaque_enough = valid && passes_opacity(f, logit);
-    // Stage the SH records of this warp's surviving Gaussians into shared
-    // memory asynchronously (16-byte copies, coalesced across the warp); the
-    // copies overlap the projection below. Records of culled lanes are skipped.
-    const uint32_t need = __ballot_sync(kFull, opaque_enough);
+    const float d = valid ? view_depth(f, x, y, z) : 0.f;
+    // Stage the SH records of the lanes that will probably be visible into
+    // shared memory asynchronously (16-byte copies, coalesced across the
+    // warp), so the copies overlap the projection below; lanes that turn out
+    // visible without the hint get their record afterwards.
+    const bool likely = opaque_enough && likely_visible(f, x, y, z, d, l0, l1, l2);
+    const uint32_t need = __ballot_sync(kFull, likely);
     float* stage = s_sh[warp];
+    const float4* src = sh + warp_first * 12;
     if (need) {
-        const float4* src = sh + warp_first * 12;
 #pragma unroll
         for (int r = 0; r < 12; ++r) {
-            const int v = lane + r * kWarp;
-            const int g = v / 12, c = v - g * 12;
-            if ((need >> g) & 1u) cp_async16(stage + g * kShPad + 4 * c, src + v);
+            const int vv = lane + r * kWarp;
+            const int g = vv / 12, c = vv - g * 12;
+            if ((need >> g) & 1u) cp_async16(stage + g * kShPad + 4 * c, src + vv);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
@@ -67,14 +70,23 @@ k_preprocess(int64_t n, const float* __restrict__ means, const float* __restrict
     bool vis = false;
     Projection P;
     if (valid) {
-        const float d = view_depth(f, x, y, z);
         depth[i] = d;
         vis = opaque_enough && d > f.znear;
         if (vis) vis = project_splat(f, x, y, z, q, l0, l1, l2, logit, P);
     }
+    const uint32_t late = __ballot_sync(kFull, vis && !likely);
+    if (late) {
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+            const int vv = lane + r * kWarp;
+            const int g = vv / 12, c = vv - g * 12;
+            if ((late >> g) & 1u) cp_async16(stage + g * kShPad + 4 * c, src + vv);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
 
     // SH colour (§2.1, §3.2) for the visible lanes from the staged records.
-    if (need) {
+    if (need | late) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
         if (vis) {

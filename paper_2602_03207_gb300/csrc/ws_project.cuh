@@ -66,6 +66,23 @@ __device__ __forceinline__ float view_depth(const Frame& f, float x, float y, fl
                      f.t[2]);
 }
 
+// Whether a Gaussian in front of the near plane (depth d) will probably be
+// visible: its projected centre inside the viewport widened by a bound on its
+// screen extent, sqrt(2 ln 255) * 1.6 * f * max scale / d plus the dilation
+// (1.6 covers the row norm of the Jacobian with the guard-band clamp). Only a
+// prefetch hint: callers still handle a visible splat it missed.
+__device__ __forceinline__ bool likely_visible(const Frame& f, float x, float y, float z, float d, float l0,
+                                               float l1, float l2) {
+    if (!(d > f.znear)) return false;
+    const float cxs = __fmaf_rn(f.R[0], x, __fmaf_rn(f.R[1], y, __fmaf_rn(f.R[2], z, f.t[0])));
+    const float cys = __fmaf_rn(f.R[3], x, __fmaf_rn(f.R[4], y, __fmaf_rn(f.R[5], z, f.t[1])));
+    const float rd = 1.f / d;
+    const float u = __fmaf_rn(f.fx * rd, cxs, f.cx), v = __fmaf_rn(f.fy * rd, cys, f.cy);
+    const float smax = expf(fmaxf(l0, fmaxf(l1, l2)));
+    const float m = 3.33f * (1.6f * fmaxf(f.fx, f.fy) * smax * rd + 0.6f) + 2.f;
+    return u > -m && u < (float)f.W + m && v > -m && v < (float)f.H + m;
+}
+
 // §3.4 opacity culling: sigma < 1/255 <=> logit < -ln 254, decided exactly.
 __device__ __forceinline__ bool passes_opacity(const Frame& f, float logit) {
     return (double)logit >= kOpacityLogitMin || (f.flags & WS_CFG_NO_OPACITY_CULL);
