@@ -8,6 +8,33 @@ namespace ws {
 
 constexpr int kBlendBatch = 256;
 
+// Bitmask of the tile's BW x BH pixel blocks (BPR per row, BROWS rows) that
+// a splat at tile-relative (x, y) can reach with alpha >= 1/255 (§3.4), i.e.
+// whose pixel centres meet the bounding box of the ellipse
+// q = a dx^2 + 2 b dx dy + c dy^2 <= qc: half-widths sqrt(qc Sigma'_xx),
+// sqrt(qc Sigma'_yy) with Sigma' = [[c, -b], [-b, a]] / det. The box carries
+// a margin (relative and absolute) well above the error of the approximate
+// reciprocal and square roots, so no pixel that the blend's own test keeps is
+// left out; a block visited without need adds w = 0.
+template <int BW, int BH, int BPR, int BROWS>
+__device__ __forceinline__ uint32_t splat_block_mask(float x, float y, float a, float b, float c, float qc) {
+    const float rdet = rcp_approx(fmaf(a, c, -b * b));
+    const float ex = sqrt_approx(qc * c * rdet) * 1.0001f + 1e-3f;
+    const float ey = sqrt_approx(qc * a * rdet) * 1.0001f + 1e-3f;
+    // blocks whose pixel centres [BW col + .5, BW col + BW - .5] x [BH row + .5, ..] meet the box
+    const float c0 = fmaxf(0.f, ceilf((x - ex - (BW - 0.5f)) * (1.f / BW)));
+    const float c1 = fminf((float)(BPR - 1), floorf((x + ex - 0.5f) * (1.f / BW)));
+    const float r0 = fmaxf(0.f, ceilf((y - ey - (BH - 0.5f)) * (1.f / BH)));
+    const float r1 = fminf((float)(BROWS - 1), floorf((y + ey - 0.5f) * (1.f / BH)));
+    uint32_t mask = 0;
+    if (c0 <= c1 && r0 <= r1) {
+        const int ic0 = (int)c0, ic1 = (int)c1, ir0 = (int)r0, ir1 = (int)r1;
+        const uint32_t row = ((2u << ic1) - 1u) & ~((1u << ic0) - 1u);
+        for (int rr = ir0; rr <= ir1; ++rr) mask |= row << (rr * BPR);
+    }
+    return mask;
+}
+
 // Shared-memory record of one splat for the blend (48 bytes).
 struct SplatRec {
     float4 geo;   // tile-relative centre x, y; conic premultiplied A, B
@@ -39,7 +66,7 @@ struct FloatSplats {
 // One block per tile. Each warp owns WPB (TS^2/256, at least 1) 8x4 pixel
 // blocks. Splats are staged 256 at a time; while staging, every splat also
 // records the bitmask of the tile's 8x4 blocks that its opacity-aware
-// extent box reaches. Each warp then walks the batch 32 splats at a time,
+// ellipse reaches (splat_block_mask). Each warp then walks the batch 32 splats at a time,
 // ballots the bit of its own block and visits only those splats, in list
 // order, so per pixel the compositing order is unchanged.
 template <int TS, typename Splats>
@@ -83,27 +110,11 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
             sp.load(g, ox, oy, r.geo.x, r.geo.y, a, b, c, op, r.col);
             r.geo.z = -0.5f * kLog2e * a;
             r.geo.w = -kLog2e * b;
-            r.geo2 = make_float4(-0.5f * kLog2e * c, log2f(op), 0.f, 0.f);
+            const float L = lg2_approx(op);
+            r.geo2 = make_float4(-0.5f * kLog2e * c, L, 0.f, 0.f);
             s_rec[j] = r;
-            // Box of the ellipse where the alpha reaches 1/255 (§3.4), with a
-            // small margin so rounding never drops a pair the per-pixel test
-            // would keep: half-widths sqrt(q_c Sigma'_xx), sqrt(q_c Sigma'_yy).
-            const float det = fmaf(a, c, -b * b);
-            const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, 2.f * (kLn255 + __logf(op)));
-            const float ex = sqrtf(qc * c / det) * 1.0001f + 1e-3f;
-            const float ey = sqrtf(qc * a / det) * 1.0001f + 1e-3f;
-            // blocks whose pixel centres [8c + .5, 8c + 7.5] x [4r + .5, 4r + 3.5] meet the box
-            const float c0 = fmaxf(0.f, ceilf((r.geo.x - ex - (BW - 0.5f)) * (1.f / BW)));
-            const float c1 = fminf((float)(BPR - 1), floorf((r.geo.x + ex - 0.5f) * (1.f / BW)));
-            const float r0 = fmaxf(0.f, ceilf((r.geo.y - ey - (BH - 0.5f)) * (1.f / BH)));
-            const float r1 = fminf((float)(BROWS - 1), floorf((r.geo.y + ey - 0.5f) * (1.f / BH)));
-            uint32_t mask = 0;
-            if (c0 <= c1 && r0 <= r1) {
-                const int ic0 = (int)c0, ic1 = (int)c1, ir0 = (int)r0, ir1 = (int)r1;
-                const uint32_t row = ((2u << ic1) - 1u) & ~((1u << ic0) - 1u);
-                for (int rr = ir0; rr <= ir1; ++rr) mask |= row << (rr * BPR);
-            }
-            s_mask[j] = mask;
+            const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, kTwoLn2 * (L - kLog2AlphaMin));
+            s_mask[j] = splat_block_mask<BW, BH, BPR, BROWS>(r.geo.x, r.geo.y, a, b, c, qc);
         }
         __syncthreads();
 #pragma unroll
@@ -245,24 +256,12 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
             r.geo.y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
             r.geo.z = -0.5f * kLog2e * a;
             r.geo.w = -kLog2e * b;
-            r.geo2 = make_float4(-0.5f * kLog2e * c, log2f(op), a, b);
+            const float L = lg2_approx(op);
+            r.geo2 = make_float4(-0.5f * kLog2e * c, L, a, b);
             r.col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), c);
             s_rec[j] = r;
-            const float det = fmaf(a, c, -b * b);
-            const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, 2.f * (kLn255 + __logf(op)));
-            const float ex = sqrtf(qc * c / det) * 1.0001f + 1e-3f;
-            const float ey = sqrtf(qc * a / det) * 1.0001f + 1e-3f;
-            const float c0 = fmaxf(0.f, ceilf((r.geo.x - ex - (BW - 0.5f)) * (1.f / BW)));
-            const float c1 = fminf((float)(BPR - 1), floorf((r.geo.x + ex - 0.5f) * (1.f / BW)));
-            const float r0 = fmaxf(0.f, ceilf((r.geo.y - ey - (BH - 0.5f)) * (1.f / BH)));
-            const float r1 = fminf((float)(BROWS - 1), floorf((r.geo.y + ey - 0.5f) * (1.f / BH)));
-            uint32_t mask = 0;
-            if (c0 <= c1 && r0 <= r1) {
-                const int ic0 = (int)c0, ic1 = (int)c1, ir0 = (int)r0, ir1 = (int)r1;
-                const uint32_t row = ((2u << ic1) - 1u) & ~((1u << ic0) - 1u);
-                for (int rr = ir0; rr <= ir1; ++rr) mask |= row << (rr * BPR);
-            }
-            s_mask[j] = mask;
+            const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, kTwoLn2 * (L - kLog2AlphaMin));
+            s_mask[j] = splat_block_mask<BW, BH, BPR, BROWS>(r.geo.x, r.geo.y, a, b, c, qc);
             const uint2 rc = __ldg(rect + g);
             const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
             s_slot[j] = slot_of(g) + (ty - y0) * (x1 - x0 + 1) + (tx - x0);

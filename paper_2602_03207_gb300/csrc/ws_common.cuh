@@ -133,6 +133,27 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// log2(x) on the special-function unit (PTX lg2.approx: absolute error about
+// 2^-22). The blends take L = log2(sigma) from it, forward and backward alike.
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/x and sqrt(x) on the special-function unit (PTX rcp.approx, sqrt.approx:
+// a few ulp). Used only where a margin absorbs the error (block masks).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kAlphaMin = 1.0f / 255.0f;  // §3.4 quantisation threshold
 constexpr float kAlphaMax = 0.99f;
@@ -150,6 +171,9 @@ constexpr double kOpacityLogitMin = -5.537334267018537;
 // blend both decide and evaluate through this function, so they agree on
 // every pair.
 constexpr float kLog2AlphaMin = -7.994353436858858f;  // log2(1/255)
+constexpr float kTwoLn2 = 1.3862943611198906f;
+// The extent threshold from L = log2(sigma): e >= log2(1/255) <=> q <= q_c
+// with q_c = 2 ln 2 (L - log2(1/255)) = 2 (ln 255 + ln sigma).
 
 __device__ __forceinline__ float splat_log2_alpha(float dx, float dy, float A, float B, float C, float L) {
     const float u = __fmaf_rn(A, dx, __fmul_rn(B, dy));
