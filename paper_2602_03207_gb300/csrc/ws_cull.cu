@@ -22,7 +22,7 @@ namespace ws {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 4;
 constexpr int kChunk = kScanThreads * kScanItems;  // Gaussians per block
 constexpr int kTopThreads = 1024;
 constexpr int kSlotCap = 4096;  // slots per chunk resolved through shared memory
@@ -92,7 +92,7 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
     const int64_t base = (int64_t)blockIdx.x * kChunk;
     const int cnt = (int)((n - base) < kChunk ? (n - base) : kChunk);
 
-    // Blocked arrangement: thread t owns Gaussians base + t*8 .. base + t*8 + 7,
+    // Blocked arrangement: thread t owns Gaussians base + t*kScanItems .. + kScanItems - 1,
     // so a thread-serial prefix plus one block scan gives the local offsets.
     uint32_t v[kScanItems];
     uint32_t acc = 0;
