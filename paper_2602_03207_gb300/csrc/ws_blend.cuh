@@ -295,7 +295,10 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
                     const float raw = ex2_approx(e);
                     const float alpha = fminf(kAlphaMax, raw);
                     any = true;
-                    const float Tb = T[k] / (1.f - alpha);
+                    // T before this pair, T_after / (1 - alpha), with the
+                    // reciprocal on the special-function unit (a few ulp;
+                    // 1 - alpha >= 0.01)
+                    const float Tb = T[k] * rcp_approx(1.f - alpha);
                     const float w = alpha * Tb;
                     float dalpha = 0.f;
                     const float cc[3] = {r.col.x, r.col.y, r.col.z};
