@@ -67,58 +67,68 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
     const uint32_t cnt = valid ? __ldg(touched + i) : 0u;
     const bool vis = cnt > 0;
 
+    // The SH records of this warp's visible Gaussians are copied into shared
+    // memory asynchronously (16-byte copies, coalesced across the warp) while
+    // the pair records are summed and the geometry adjoint runs.
+    const int64_t warp_first = (int64_t)blockIdx.x * kPbThreads + warp * kWarp;
+    float* stage = s_sh[warp];
+    const uint32_t need = __ballot_sync(kFull, vis);
+    if (need) {
+        const float4* src = sh + warp_first * 12;
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+            const int v = lane + r * kWarp;
+            const int g = v / 12, c = v - g * 12;
+            if ((need >> g) & 1u) cp_async16(stage + g * kShPad + 4 * c, src + v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+
     float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
     float pr[kPart];
 #pragma unroll
     for (int c = 0; c < kPart; ++c) pr[c] = 0.f;
     float X[3] = {0.f, 0.f, 0.f};
+    float col[3] = {0.f, 0.f, 0.f};
     if (vis) {
-        // slot-ordered sum of this Gaussian's pair records
-        const float* src = partials + (size_t)__ldg(offsets + i) * kPart;
-        for (uint32_t s = 0; s < cnt; ++s)
-#pragma unroll
-            for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
+        const uint32_t first = __ldg(offsets + i);
         X[0] = __ldg(means + 3 * i);
         X[1] = __ldg(means + 3 * i + 1);
         X[2] = __ldg(means + 3 * i + 2);
         const float sig = __ldg(opacity + i);
-        glogit = pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
-
         const float4 q4 = __ldg(quats + i);
         const float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1), __ldg(log_scales + 3 * i + 2)};
+        col[0] = __ldg(rgb + 3 * i);
+        col[1] = __ldg(rgb + 3 * i + 1);
+        col[2] = __ldg(rgb + 3 * i + 2);
+        // slot-ordered sum of this Gaussian's pair records
+        const float* src = partials + (size_t)first * kPart;
+        for (uint32_t s = 0; s < cnt; ++s)
+#pragma unroll
+            for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
+        glogit = pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
         splat_adjoint(f, X, q4, ls, pr, gm, gls, gq);
     }
 
-    // SH colour adjoint with warp-staged (coalesced) SH reads and gradient writes.
-    const int64_t warp_first = (int64_t)blockIdx.x * kPbThreads + warp * kWarp;
-    float* stage = s_sh[warp];
+    // SH colour adjoint; gradients staged back through shared memory for
+    // coalesced writes (zeros for Gaussians that are not visible).
     const int64_t avail = n - warp_first;
     const int nvec = avail <= 0 ? 0 : (int)(avail >= kWarp ? kWarp * 12 : avail * 12);
-    const bool any_vis = __any_sync(kFull, vis);
-    if (any_vis) {
-        const float4* src = sh + warp_first * 12;
-#pragma unroll
-        for (int r = 0; r < 12; ++r) {
-            const int v = lane + r * kWarp;
-            if (v < nvec) {
-                const int g = v / 12, c = v - g * 12;
-                *reinterpret_cast<float4*>(stage + g * kShPad + 4 * c) = __ldg(src + v);
-            }
-        }
+    if (need) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
     }
     float* mine = stage + lane * kShPad;
     if (vis) {
-        const float col[3] = {__ldg(rgb + 3 * i), __ldg(rgb + 3 * i + 1), __ldg(rgb + 3 * i + 2)};
         float gsh[48];
         sh_adjoint(f, X, mine, col, pr, gm, gsh, false);
 #pragma unroll
         for (int k = 0; k < 48; ++k) mine[k] = gsh[k];
-    } else if (any_vis) {
+    } else if (need) {
 #pragma unroll
         for (int k = 0; k < 48; ++k) mine[k] = 0.f;
     }
-    if (any_vis) {
+    if (need) {
         __syncwarp();
         float4* dst = d_sh + warp_first * 12;
 #pragma unroll

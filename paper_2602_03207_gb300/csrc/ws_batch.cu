@@ -186,14 +186,22 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
         __syncwarp();
     }
     float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
+    // The next view's pair count and first slot are loaded one view ahead, so
+    // their latency overlaps this view's adjoint.
+    uint32_t cnt_next = valid ? __ldg(touched + i) : 0u;
+    uint32_t off_next = valid ? __ldg(offsets + i) : 0u;
     for (int v = 0; v < ft.views; ++v) {
         const int64_t o = (int64_t)v * n + i;
-        const uint32_t cnt = valid ? __ldg(touched + o) : 0u;
+        const uint32_t cnt = cnt_next, first = off_next;
+        if (valid && v + 1 < ft.views) {
+            cnt_next = __ldg(touched + o + n);
+            off_next = __ldg(offsets + o + n);
+        }
         if (cnt == 0) continue;
         float pr[kPart];
 #pragma unroll
         for (int c = 0; c < kPart; ++c) pr[c] = 0.f;
-        const float* src = partials + (size_t)__ldg(offsets + o) * kPart;
+        const float* src = partials + (size_t)first * kPart;
         for (uint32_t s = 0; s < cnt; ++s)
 #pragma unroll
             for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
