@@ -85,3 +85,37 @@ def test_key_layout_host_logic():
     assert render.key_end_bit(3840, 2160, 16) == 31 + 15
     assert render.key_end_bit(256, 256, 16) == 31 + 8
     assert render.key_end_bit(16, 16, 16) == 31
+
+
+def test_null_device_pointers_are_rejected(lib):
+    """Every compute entry point, called with a positive count, valid camera
+    and configuration and null device pointers, returns WS_ERR_INVALID_ARG
+    before touching the GPU."""
+    from paper_2602_03207_gb300 import capi
+    from paper_2602_03207_gb300 import synthetic as S
+    cam = capi.camera(S.small_forward()[1])
+    cfg = capi.config()
+    names = ["ws_preprocess", "ws_cull", "ws_sort", "ws_rasterize", "ws_preprocess_packed",
+             "ws_rasterize_packed", "ws_render_quads", "ws_rasterize_backward", "ws_sort_noalloc",
+             "ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
+             "ws_image_residual", "ws_read_status"]
+    for nm in names:
+        fn = getattr(lib, nm)
+        args = []
+        ints32 = iter([0, 40, 8] if nm.startswith("ws_sort") else [])  # begin, end, digit bits
+        for t in fn.argtypes:
+            if t is C.c_int64:
+                args.append(16)
+            elif t is C.c_int32:
+                args.append(next(ints32, 1))
+            elif t is C.POINTER(C.c_int32):
+                args.append(C.byref(C.c_int32(0)))
+            elif t is C.POINTER(C.c_uint32):
+                args.append(C.byref(C.c_uint32(0)))
+            elif "camera" in repr(t).lower():
+                args.append(C.byref(cam))
+            elif "config" in repr(t).lower():
+                args.append(C.byref(cfg))
+            else:
+                args.append(None)
+        assert fn(*args) == capi.WS_ERR_INVALID_ARG, nm
