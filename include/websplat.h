@@ -123,7 +123,8 @@ size_t ws_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera *cam,
  *   rgb[n][3], opacity[n] (sigma)
  *   rect[n][4]    uint16 tile rectangle x0, y0, x1, y1 (inclusive)
  *   tiles_touched[n]  uint32 tiles in rect; 0 means culled
- * For a culled Gaussian only depth and tiles_touched are written. */
+ * Every entry is written; a culled Gaussian gets tiles_touched = 0 and
+ * zeros in mean2d, conic, rgb, opacity and rect. */
 ws_status ws_preprocess(int64_t n, const float *means, const float *log_scales,
                         const float *quats, const float *opacity_logits, const float *sh,
                         const ws_camera *cam, const ws_config *cfg,
@@ -252,7 +253,8 @@ ws_status ws_rasterize(const uint32_t *num_keys, const uint64_t *keys, const uin
  *                 (Sigma' = v1 v1^T + v2 v2^T), rounded to nearest even
  *   rgba[n]       uint32: r | g << 8 | b << 16 | sigma << 24, each
  *                 round(255 clamp(x, 0, 1)) (colours above 1 are clamped)
- * and depth, rect and tiles_touched as ws_preprocess, with the extent, the
+ * (every entry written, zeros for a culled Gaussian) and depth, rect and
+ * tiles_touched as ws_preprocess, with the extent, the
  * viewport test and the tile rectangle computed from the packed sigma and
  * axes. ws_cull and ws_sort take the outputs unchanged; ws_rasterize_packed
  * reads the packed record. Images differ from the float path by the
@@ -335,7 +337,8 @@ ws_status ws_rasterize_backward(int64_t n, const float *means, const float *log_
  * the per-Gaussian layouts of the single-view calls (mean2d[V][n][4],
  * conic[V][n][3], depth[V][n], rgb[V][n][3], rect[V][n][4],
  * tiles_touched[V][n], offsets[V * n + 1]); opacity[n] is shared by all
- * views. Tiles are numbered in one global grid: view v's tiles follow those
+ * views (0 for a Gaussian visible in none). Every entry is written, with
+ * zeros for a (view, Gaussian) that is culled, as in ws_preprocess. Tiles are numbered in one global grid: view v's tiles follow those
  * of views 0..v-1, and the keys carry that global tile id (sort bits [0, 31 +
  * ceil(log2 total tiles))). Images are packed: view v's H_v x W_v x 3 floats
  * start after those of views 0..v-1 (likewise t_final and n_contrib).

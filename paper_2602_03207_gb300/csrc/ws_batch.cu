@@ -80,25 +80,28 @@ k_preprocess_batch(int64_t n, const float* __restrict__ means, const float* __re
             vis = opaque_enough && d > f.znear;
             if (vis) vis = project_splat(f, x, y, z, q, l0, l1, l2, logit, P);
         }
+        float3 c3 = make_float3(0.f, 0.f, 0.f);
         if (vis) {
             const float dx = x - f.campos[0], dy = y - f.campos[1], dz = z - f.campos[2];
             const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-            float3 c3;
             sh_eval(dx * inv, dy * inv, dz * inv, stage + lane * kShPad, c3);
-            mean2d[o] = P.m4;
-            conic[3 * o] = P.ca;
-            conic[3 * o + 1] = P.cb;
-            conic[3 * o + 2] = P.cc;
-            rgb[3 * o] = c3.x;
-            rgb[3 * o + 1] = c3.y;
-            rgb[3 * o + 2] = c3.z;
-            rect[o] = make_uint2(P.x0 | (P.y0 << 16), P.x1 | (P.y1 << 16));
             sigma = P.sigma;
             any_view = true;
         }
-        if (valid) tiles_touched[o] = vis ? (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1) : 0u;
+        // every lane stores its entries (zeros where culled): whole sectors
+        if (valid) {
+            mean2d[o] = vis ? P.m4 : make_float4(0.f, 0.f, 0.f, 0.f);
+            conic[3 * o] = vis ? P.ca : 0.f;
+            conic[3 * o + 1] = vis ? P.cb : 0.f;
+            conic[3 * o + 2] = vis ? P.cc : 0.f;
+            rgb[3 * o] = c3.x;
+            rgb[3 * o + 1] = c3.y;
+            rgb[3 * o + 2] = c3.z;
+            rect[o] = vis ? make_uint2(P.x0 | (P.y0 << 16), P.x1 | (P.y1 << 16)) : make_uint2(0u, 0u);
+            tiles_touched[o] = vis ? (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1) : 0u;
+        }
     }
-    if (any_view) opacity[i] = sigma;
+    if (valid) opacity[i] = any_view ? sigma : 0.f;
 }
 
 template <int TS>

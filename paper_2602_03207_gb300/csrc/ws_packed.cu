@@ -181,6 +181,7 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
+    uint32_t packed_rgba = 0u;
     if (need | late) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
@@ -189,13 +190,18 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
             const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
             float3 c3;
             sh_eval(dx * inv, dy * inv, dz * inv, stage + lane * kShPad, c3);
-            mean2d[i] = make_float2(P.m4.x, P.m4.y);
-            axes[i] = ax;
-            rgba[i] = quant8(c3.x) | (quant8(c3.y) << 8) | (quant8(c3.z) << 16) | (a8 << 24);
-            rect[i] = make_uint2(P.x0 | (P.y0 << 16), P.x1 | (P.y1 << 16));
+            packed_rgba = quant8(c3.x) | (quant8(c3.y) << 8) | (quant8(c3.z) << 16) | (a8 << 24);
         }
     }
-    if (valid) tiles_touched[i] = vis ? (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1) : 0u;
+    // Every lane stores its entries (zeros for a culled Gaussian): whole
+    // sectors, no read of partly written ones from DRAM (as in ws_preprocess).
+    if (valid) {
+        mean2d[i] = vis ? make_float2(P.m4.x, P.m4.y) : make_float2(0.f, 0.f);
+        axes[i] = vis ? ax : make_uint2(0u, 0u);
+        rgba[i] = packed_rgba;
+        rect[i] = vis ? make_uint2(P.x0 | (P.y0 << 16), P.x1 | (P.y1 << 16)) : make_uint2(0u, 0u);
+        tiles_touched[i] = vis ? (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1) : 0u;
+    }
 }
 
 template <int TS>

@@ -2,9 +2,10 @@
 // and the opacity culling and opacity-aware extent of §3.4).
 //
 // One thread per Gaussian, 128-thread blocks. HBM-bound: 236 B of input per
-// visible Gaussian (59 floats), 44 B per opacity-culled one (everything but
-// the SH). The 192-byte SH record is the bulk of the traffic; each warp
-// copies the SH of its surviving Gaussians into shared memory with
+// visible Gaussian (59 floats), 16 B per opacity-culled one (logit, centre),
+// 44 B per one culled later (no SH); 60 B of output each. The 192-byte SH
+// record is the bulk of the traffic; each warp copies the SH of its
+// Gaussians that will probably be visible into shared memory with
 // asynchronous, coalesced 16-byte copies issued before the projection math
 // (a per-thread load of a 192-byte stride would touch 32 cache lines per
 // instruction), padded to 52 floats so the per-lane float4 reads are
@@ -86,26 +87,31 @@ k_preprocess(int64_t n, const float* __restrict__ means, const float* __restrict
     }
 
     // SH colour (§2.1, §3.2) for the visible lanes from the staged records.
+    float3 c3 = make_float3(0.f, 0.f, 0.f);
     if (need | late) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
         if (vis) {
             const float dx = x - f.campos[0], dy = y - f.campos[1], dz = z - f.campos[2];
             const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-            float3 c3;
             sh_eval(dx * inv, dy * inv, dz * inv, stage + lane * kShPad, c3);
-            mean2d[i] = P.m4;
-            conic[3 * i] = P.ca;
-            conic[3 * i + 1] = P.cb;
-            conic[3 * i + 2] = P.cc;
-            rgb[3 * i] = c3.x;
-            rgb[3 * i + 1] = c3.y;
-            rgb[3 * i + 2] = c3.z;
-            opacity[i] = P.sigma;
-            rect[i] = make_uint2(P.x0 | (P.y0 << 16), P.x1 | (P.y1 << 16));
         }
     }
-    if (valid) tiles_touched[i] = vis ? (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1) : 0u;
+    // Every lane stores its entries (zeros for a culled Gaussian), so the
+    // warp writes whole 32-byte sectors: a sector left partly written would
+    // cost a read of it from DRAM when it leaves the L2.
+    if (valid) {
+        mean2d[i] = vis ? P.m4 : make_float4(0.f, 0.f, 0.f, 0.f);
+        conic[3 * i] = vis ? P.ca : 0.f;
+        conic[3 * i + 1] = vis ? P.cb : 0.f;
+        conic[3 * i + 2] = vis ? P.cc : 0.f;
+        rgb[3 * i] = c3.x;
+        rgb[3 * i + 1] = c3.y;
+        rgb[3 * i + 2] = c3.z;
+        opacity[i] = vis ? P.sigma : 0.f;
+        rect[i] = vis ? make_uint2(P.x0 | (P.y0 << 16), P.x1 | (P.y1 << 16)) : make_uint2(0u, 0u);
+        tiles_touched[i] = vis ? (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1) : 0u;
+    }
 }
 
 }  // namespace
