@@ -107,10 +107,16 @@ __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
 }
 
 // Bitonic sorting network over the warp's 32*K values, element e = lane*K + k
-// in register k of lane `lane`; ascending on return.
+// in register k of lane `lane`; ascending on return. The values are
+// distinct (the sort key carries the input index), so each compare-exchange
+// is one 64-bit comparison whose outcome, xor the direction, picks the
+// element to keep. For the stages whose partner is in another lane
+// (j >= K), the direction depends on the lane only: bits j and `size` of
+// e = lane*K + k are those of lane*K, since k < K <= j.
 template <int K>
 __device__ __forceinline__ void warp_bitonic(uint64_t (&v)[K]) {
     const int lane = threadIdx.x & 31;
+    const int lk = lane * K;
     constexpr int N = kWarp * K;
 #pragma unroll
     for (int size = 2; size <= N; size <<= 1) {
@@ -120,19 +126,18 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&v)[K]) {
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     if (k & j) continue;
-                    const bool up = ((lane * K + k) & size) == 0;
+                    const bool up = ((lk + k) & size) == 0;
                     const uint64_t x = v[k], y = v[k | j];
-                    const bool swap = up ? (x > y) : (x < y);
+                    const bool swap = (x > y) == up;
                     v[k] = swap ? y : x;
                     v[k | j] = swap ? x : y;
                 }
             } else {  // partner in lane ^ (j / K), same register
+                const bool keep_min = ((lk & j) == 0) == ((lk & size) == 0);
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    const int e = lane * K + k;
                     const uint64_t o = shfl_xor64(v[k], j / K);
-                    const bool keep_min = ((e & j) == 0) == ((e & size) == 0);
-                    v[k] = keep_min ? (o < v[k] ? o : v[k]) : (o > v[k] ? o : v[k]);
+                    v[k] = ((o < v[k]) == keep_min) ? o : v[k];
                 }
             }
         }
