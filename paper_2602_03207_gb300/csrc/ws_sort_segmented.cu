@@ -90,12 +90,12 @@ __device__ __forceinline__ void warp_rank(const uint64_t (&key)[kSegItems], int 
         const bool ok = valid_base + k * kWarp + lane < n;
         const uint32_t d = ok ? (uint32_t)(key[k] >> shift) & mask : 0u;
         const uint32_t peers = warp_match_digit<kLocalBits>(d, ok);
-        const int leader = __ffs(peers) - 1;
-        uint32_t prior = 0;
-        if (lane == leader && ok) prior = cnt[d];
-        prior = __shfl_sync(kFull, prior, leader);
+        // every lane of a digit group reads the group's running count (one
+        // broadcast address per group); its first lane then advances it
+        const uint32_t prior = ok ? cnt[d] : 0u;
         rnk[k] = prior + __popc(peers & lt);
-        if (lane == leader && ok) cnt[d] = prior + __popc(peers);
+        __syncwarp();  // every read before the update
+        if (ok && (peers & lt) == 0u) cnt[d] = prior + __popc(peers);
         __syncwarp();
     }
 }
