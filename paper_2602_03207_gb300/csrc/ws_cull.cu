@@ -86,7 +86,7 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
     __shared__ uint2 s_rect[kChunk];
     __shared__ uint32_t s_depth[kChunk];
     __shared__ uint32_t s_red[kScanThreads / 32 + 1];
-    __shared__ uint16_t s_owner[kSlotCap];  // slot -> local Gaussian (fast path; < kChunk)
+    __shared__ __align__(16) uint16_t s_owner[kSlotCap];  // slot -> local Gaussian (fast path; < kChunk)
     pdl_wait();
     pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * kChunk;
@@ -134,13 +134,20 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
             if (li < cnt && v[k] > 0) s_owner[s_off[li]] = (uint16_t)li;
         }
         __syncthreads();
-        // running maximum over the slots: thread-serial over kSlotPer slots, then a block scan
+        // running maximum over the slots: thread-serial over kSlotPer slots
+        // (read and written as 16-byte vectors: a thread's slots span 32
+        // bytes, so element-wise accesses of a warp would fall 8 to a bank),
+        // then a block scan
         constexpr int kSlotPer = kSlotCap / kScanThreads;
+        static_assert(kSlotPer == 16, "two 16-byte vectors of slots per thread");
+        uint4* own4 = reinterpret_cast<uint4*>(s_owner) + threadIdx.x * 2;
+        const uint4 o0 = own4[0], o1 = own4[1];
+        uint32_t ow[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
         uint32_t m = 0;
 #pragma unroll
         for (int k = 0; k < kSlotPer; ++k) {
             const int e = threadIdx.x * kSlotPer + k;
-            if (e < (int)total) m = max(m, (uint32_t)s_owner[e]);
+            if (e < (int)total) m = max(m, (ow[k >> 1] >> ((k & 1) * 16)) & 0xffffu);
         }
         // exclusive block max-scan of the per-thread maxima
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -161,10 +168,13 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
         for (int k = 0; k < kSlotPer; ++k) {
             const int e = threadIdx.x * kSlotPer + k;
             if (e < (int)total) {
-                prev = max(prev, (uint32_t)s_owner[e]);
-                s_owner[e] = (uint16_t)prev;
+                const int sh = (k & 1) * 16;
+                prev = max(prev, (ow[k >> 1] >> sh) & 0xffffu);
+                ow[k >> 1] = (ow[k >> 1] & ~(0xffffu << sh)) | (prev << sh);
             }
         }
+        own4[0] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+        own4[1] = make_uint4(ow[4], ow[5], ow[6], ow[7]);
         __syncthreads();
     }
     for (uint32_t s = threadIdx.x; s < total; s += kScanThreads) {
