@@ -21,17 +21,17 @@ __device__ __forceinline__ uint32_t splat_block_mask(float x, float y, float a, 
     const float rdet = rcp_approx(fmaf(a, c, -b * b));
     const float ex = sqrt_approx(qc * c * rdet) * 1.0001f + 1e-3f;
     const float ey = sqrt_approx(qc * a * rdet) * 1.0001f + 1e-3f;
-    // blocks whose pixel centres [BW col + .5, BW col + BW - .5] x [BH row + .5, ..] meet the box
-    const float c0 = fmaxf(0.f, ceilf((x - ex - (BW - 0.5f)) * (1.f / BW)));
-    const float c1 = fminf((float)(BPR - 1), floorf((x + ex - 0.5f) * (1.f / BW)));
-    const float r0 = fmaxf(0.f, ceilf((y - ey - (BH - 0.5f)) * (1.f / BH)));
-    const float r1 = fminf((float)(BROWS - 1), floorf((y + ey - 0.5f) * (1.f / BH)));
+    // blocks whose pixel centres [BW col + .5, BW col + BW - .5] x [BH row + .5, ..]
+    // meet the box: one compare pair per block column and per block row
+    const float xl = x - ex, xh = x + ex, yl = y - ey, yh = y + ey;
+    uint32_t cols = 0;
+#pragma unroll
+    for (int c = 0; c < BPR; ++c)
+        cols |= (xl <= (float)(c * BW) + (BW - 0.5f) && xh >= (float)(c * BW) + 0.5f) ? (1u << c) : 0u;
     uint32_t mask = 0;
-    if (c0 <= c1 && r0 <= r1) {
-        const int ic0 = (int)c0, ic1 = (int)c1, ir0 = (int)r0, ir1 = (int)r1;
-        const uint32_t row = ((2u << ic1) - 1u) & ~((1u << ic0) - 1u);
-        for (int rr = ir0; rr <= ir1; ++rr) mask |= row << (rr * BPR);
-    }
+#pragma unroll
+    for (int r = 0; r < BROWS; ++r)
+        mask |= (yl <= (float)(r * BH) + (BH - 0.5f) && yh >= (float)(r * BH) + 0.5f) ? (cols << (r * BPR)) : 0u;
     return mask;
 }
 
