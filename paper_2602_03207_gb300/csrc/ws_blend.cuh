@@ -21,18 +21,7 @@ __device__ __forceinline__ uint32_t splat_block_mask(float x, float y, float a, 
     const float rdet = rcp_approx(fmaf(a, c, -b * b));
     const float ex = sqrt_approx(qc * c * rdet) * 1.0001f + 1e-3f;
     const float ey = sqrt_approx(qc * a * rdet) * 1.0001f + 1e-3f;
-    // blocks whose pixel centres [BW col + .5, BW col + BW - .5] x [BH row + .5, ..]
-    // meet the box: one compare pair per block column and per block row
-    const float xl = x - ex, xh = x + ex, yl = y - ey, yh = y + ey;
-    uint32_t cols = 0;
-#pragma unroll
-    for (int c = 0; c < BPR; ++c)
-        cols |= (xl <= (float)(c * BW) + (BW - 0.5f) && xh >= (float)(c * BW) + 0.5f) ? (1u << c) : 0u;
-    uint32_t mask = 0;
-#pragma unroll
-    for (int r = 0; r < BROWS; ++r)
-        mask |= (yl <= (float)(r * BH) + (BH - 0.5f) && yh >= (float)(r * BH) + 0.5f) ? (cols << (r * BPR)) : 0u;
-    return mask;
+    return box_block_mask<BW, BH, BPR, BROWS>(x - ex, x + ex, y - ey, y + ey);
 }
 
 // Shared-memory record of one splat for the blend (48 bytes).

@@ -243,6 +243,24 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Bitmask of a tile's BW x BH pixel blocks (BPR per row, BROWS rows, bit
+// row * BPR + col) whose pixel centres [BW col + .5, BW col + BW - .5] x
+// [BH row + .5, BH row + BH - .5] meet the box [xl, xh] x [yl, yh]
+// (tile-relative): one compare pair per block column and per block row.
+template <int BW, int BH, int BPR, int BROWS>
+__device__ __forceinline__ uint32_t box_block_mask(float xl, float xh, float yl, float yh) {
+    static_assert(BPR * BROWS <= 32, "block mask is 32 bits");
+    uint32_t cols = 0;
+#pragma unroll
+    for (int c = 0; c < BPR; ++c)
+        cols |= (xl <= (float)(c * BW) + (BW - 0.5f) && xh >= (float)(c * BW) + 0.5f) ? (1u << c) : 0u;
+    uint32_t mask = 0;
+#pragma unroll
+    for (int r = 0; r < BROWS; ++r)
+        mask |= (yl <= (float)(r * BH) + (BH - 0.5f) && yh >= (float)(r * BH) + 0.5f) ? (cols << (r * BPR)) : 0u;
+    return mask;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

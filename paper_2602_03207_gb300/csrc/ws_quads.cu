@@ -186,16 +186,7 @@ k_blend_quads(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ran
             st.cb = __ldg(rgb + 3 * g + 2);
             st.pad = 0.f;
             s_q[j] = st;
-            const float c0 = fmaxf(0.f, ceilf((st.cx - q.hx - (BW - 0.5f)) * (1.f / BW)));
-            const float c1 = fminf((float)(BPR - 1), floorf((st.cx + q.hx - 0.5f) * (1.f / BW)));
-            const float r0 = fmaxf(0.f, ceilf((st.cy - q.hy - (BH - 0.5f)) * (1.f / BH)));
-            const float r1 = fminf((float)(BROWS - 1), floorf((st.cy + q.hy - 0.5f) * (1.f / BH)));
-            uint32_t mask = 0;
-            if (c0 <= c1 && r0 <= r1) {
-                const uint32_t row = ((2u << (int)c1) - 1u) & ~((1u << (int)c0) - 1u);
-                for (int rr = (int)r0; rr <= (int)r1; ++rr) mask |= row << (rr * BPR);
-            }
-            s_mask[j] = mask;
+            s_mask[j] = box_block_mask<BW, BH, BPR, BROWS>(st.cx - q.hx, st.cx + q.hx, st.cy - q.hy, st.cy + q.hy);
         }
         __syncthreads();
 #pragma unroll
