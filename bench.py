@@ -36,7 +36,7 @@ METRICS = {"hd": METRIC, "uhd": "2160p frames/s at 6M splats"}
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel on the hd workload (profiles/kernels_hd_1080p_1M.md); to be reset
 # to None whenever that kernel changes.
-KERNEL_TRAFFIC = {("k_blend", 16): 51_437_056 + 16_580_608}
+KERNEL_TRAFFIC = {("k_blend", 16): 51_419_648 + 16_329_216}
 STAGES = ("preprocess", "cull", "sort", "rasterize")
 
 
