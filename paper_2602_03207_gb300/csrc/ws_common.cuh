@@ -261,6 +261,47 @@ __device__ __forceinline__ uint32_t box_block_mask(float xl, float xh, float yl,
     return mask;
 }
 
+// Segment boundaries of a sorted key list of n keys, warp-cooperatively over
+// a grid-stride loop. The segment id of position i is seg_of(keys[i]) for
+// i < n, -1 before the list and end_id at i = n (ids are non-decreasing).
+// For every position i in [0, n] whose id c exceeds the previous position's
+// id a, the whole warp calls fill(a, c, i) and shares the ids a..c among its
+// lanes, so a long run of empty segments does not serialise one thread. Each
+// lane issues U independent key loads before using any of them.
+template <int U, typename SegOf, typename Fill>
+__device__ __forceinline__ void scan_boundaries(const uint64_t* __restrict__ keys, uint32_t n, int64_t end_id,
+                                                SegOf seg_of, Fill fill) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    constexpr int64_t kSpan = (int64_t)kWarp * U;
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * kSpan <= (int64_t)n;
+         w += warps) {
+        const int64_t base = w * kSpan;
+        int64_t id[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + u * kWarp + lane;
+            id[u] = i < (int64_t)n ? seg_of(__ldg(keys + i)) : end_id;
+        }
+        int64_t prev = base == 0 ? -1 : seg_of(__ldg(keys + base - 1));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + u * kWarp + lane;
+            const int64_t c = id[u];
+            int64_t a = __shfl_up_sync(kFull, c, 1);
+            if (lane == 0) a = prev;
+            prev = __shfl_sync(kFull, c, 31);
+            uint32_t todo = __ballot_sync(kFull, i <= (int64_t)n && c > a);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                fill(__shfl_sync(kFull, a, src), __shfl_sync(kFull, c, src),
+                     (uint32_t)__shfl_sync(kFull, (uint32_t)i, src));
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

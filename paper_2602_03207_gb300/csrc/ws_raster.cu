@@ -30,38 +30,25 @@ constexpr int kRangeThreads = 256;
 // ranges[t] = [start, end) of tile t in the sorted key list, for every tile
 // (an empty tile gets start = end), in one pass over positions 0..n: at
 // position i, between the tiles a of key i-1 and c of key i, tiles a+1..c
-// start and tiles a..c-1 end. The warp fills its lanes' runs of tiles
-// together, so a long run of empty tiles does not serialise one thread.
-// Keys whose tile is >= ntiles (none in a frame) count as past the end.
+// start and tiles a..c-1 end (scan_boundaries). Keys whose tile is >= ntiles
+// (none in a frame) count as past the end. The blend is allowed to launch
+// only once this scan is done (the trigger is at the end): its blocks do not
+// wait on the SMs while the scan runs.
 __global__ void __launch_bounds__(kRangeThreads)
 k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys,
               uint2* __restrict__ ranges, uint32_t ntiles) {
     pdl_wait();
-    pdl_trigger();
-    const uint32_t n = *num_keys;
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * kRangeThreads;
-    for (int64_t base = (int64_t)blockIdx.x * kRangeThreads + (threadIdx.x & ~31); base <= (int64_t)n;
-         base += stride) {
-        const int64_t i = base + lane;
-        int64_t c = (int64_t)ntiles;
-        if (i < (int64_t)n) c = min((int64_t)(__ldg(keys + i) >> 31), (int64_t)ntiles);
-        int64_t a = __shfl_up_sync(kFull, c, 1);
-        if (lane == 0) a = i == 0 ? -1 : min((int64_t)(__ldg(keys + i - 1) >> 31), (int64_t)ntiles);
-        if (i == 0) a = -1;
-        if (i > (int64_t)n) a = c;  // past the count: nothing to write
-        uint32_t todo = __ballot_sync(kFull, c > a);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t lo = __shfl_sync(kFull, a, src), hi = __shfl_sync(kFull, c, src);
-            const uint32_t pos = (uint32_t)__shfl_sync(kFull, (uint32_t)i, src);
+    const int64_t nt = (int64_t)ntiles;
+    scan_boundaries<4>(
+        keys, *num_keys, nt, [nt](uint64_t k) { return min((int64_t)(k >> 31), nt); },
+        [&](int64_t lo, int64_t hi, uint32_t pos) {
             for (int64_t t = lo + lane; t <= hi; t += kWarp) {
-                if (t >= 0 && t < hi && t < (int64_t)ntiles) ranges[t].y = pos;
-                if (t > lo && t < (int64_t)ntiles) ranges[t].x = pos;
+                if (t >= 0 && t < hi && t < nt) ranges[t].y = pos;
+                if (t > lo && t < nt) ranges[t].x = pos;
             }
-        }
-    }
+        });
+    pdl_trigger();
 }
 
 template <int TS>

@@ -38,30 +38,20 @@ constexpr int kSplitBit = 31;                     // segment id above, sub-key b
 constexpr int kMaxSegBits = 24;
 
 // start[s] for s in (seg(i-1), seg(i)]: the first position of every segment,
-// empty ones included; start[nseg] = n. One thread per position 0..n; the
-// warp fills its lanes' runs of segment ids together, 32 entries at a time,
-// so a long run of empty segments does not serialise one thread.
+// empty ones included; start[nseg] = n (scan_boundaries over positions 0..n).
+// The local sorts are allowed to launch only once this scan is done.
 __global__ void __launch_bounds__(256)
 k_seg_bounds(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, uint32_t seg_mask,
              uint32_t nseg, uint32_t* __restrict__ start) {
     pdl_wait();
-    pdl_trigger();
-    const uint32_t n = *num_keys;
     const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t a = 0, c = 0;  // this lane writes start[a + 1 .. c]
-    if (i <= (int64_t)n) {
-        a = i == 0 ? -1 : (int64_t)((uint32_t)(keys[i - 1] >> kSplitBit) & seg_mask);
-        c = i == (int64_t)n ? (int64_t)nseg : (int64_t)((uint32_t)(keys[i] >> kSplitBit) & seg_mask);
-    }
-    uint32_t todo = __ballot_sync(kFull, c > a);
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int64_t lo = __shfl_sync(kFull, a, src) + 1, hi = __shfl_sync(kFull, c, src);
-        const uint32_t pos = (uint32_t)__shfl_sync(kFull, (uint32_t)i, src);
-        for (int64_t s = lo + lane; s <= hi; s += kWarp) start[s] = pos;
-    }
+    scan_boundaries<4>(
+        keys, *num_keys, (int64_t)nseg,
+        [seg_mask](uint64_t k) { return (int64_t)((uint32_t)(k >> kSplitBit) & seg_mask); },
+        [&](int64_t lo, int64_t hi, uint32_t pos) {
+            for (int64_t s = lo + 1 + lane; s <= hi; s += kWarp) start[s] = pos;
+        });
+    pdl_trigger();
 }
 
 __device__ __forceinline__ uint32_t sub_key(uint64_t k, int begin_bit, uint32_t sub_mask) {
@@ -510,8 +500,11 @@ cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity
     uint32_t* ov = part_alt ? vals : vals_alt;
     uint32_t* start = static_cast<uint32_t*>(scratch) + seg_start_offset_words(key_capacity);
     const uint32_t nseg = 1u << seg_bits;
-    const int64_t threads = key_capacity + 1;
-    e = launch_pdl(k_seg_bounds, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, stream,
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t spans = (key_capacity + 1 + 1023) / 1024;
+    e = launch_pdl(k_seg_bounds, dim3((unsigned)(spans < sms * 8 ? spans : sms * 8)), dim3(256), 0, stream,
                    (const uint64_t*)pk, num_keys, nseg - 1u, nseg, start);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_seg_sort, dim3(nseg + (nseg + kSegWarps - 1) / kSegWarps), dim3(kSegThreads), 0, stream, pk, pv,
