@@ -43,7 +43,6 @@ k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
             const float* __restrict__ t_final, const uint32_t* __restrict__ n_contrib,
             const float* __restrict__ d_image, float* __restrict__ partials) {
     pdl_wait();
-    pdl_trigger();
     blend_bwd_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, mean2d, conic, opacity, rgb, rect,
                        [offsets](uint32_t g) { return __ldg(offsets + g); }, t_final, n_contrib, d_image, partials);
 }
@@ -63,7 +62,6 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
     const int64_t i = (int64_t)blockIdx.x * kPbThreads + threadIdx.x;
     const bool valid = i < n;
     pdl_wait();
-    pdl_trigger();
     const uint32_t cnt = valid ? __ldg(touched + i) : 0u;
     const bool vis = cnt > 0;
 

@@ -38,7 +38,6 @@ k_preprocess_batch(int64_t n, const float* __restrict__ means, const float* __re
     const bool valid = i < n;
     const int64_t warp_first = (int64_t)blockIdx.x * kBatchThreads + warp * kWarp;
     pdl_wait();
-    pdl_trigger();
 
     float logit = 0.f, x = 0.f, y = 0.f, z = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -111,7 +110,6 @@ k_blend_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ val
               const float* __restrict__ opacity, const float* __restrict__ rgb, const FrameTable ft,
               float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
     pdl_wait();
-    pdl_trigger();
     const uint32_t t = blockIdx.x;
     const int v = view_of_tile(ft.tile_off, ft.views, t);
     const uint64_t vo = (uint64_t)v * (uint64_t)n, po = ft.pix_off[v];
@@ -129,7 +127,6 @@ k_blend_bwd_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__
                   const uint32_t* __restrict__ n_contrib, const float* __restrict__ d_image,
                   float* __restrict__ partials) {
     pdl_wait();
-    pdl_trigger();
     const uint32_t t = blockIdx.x;
     const int v = view_of_tile(ft.tile_off, ft.views, t);
     const uint64_t vo = (uint64_t)v * (uint64_t)n, po = ft.pix_off[v];
@@ -156,7 +153,6 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
     const int64_t avail = n - warp_first;
     const int nvec = avail <= 0 ? 0 : (int)(avail >= kWarp ? kWarp * 12 : avail * 12);
     pdl_wait();
-    pdl_trigger();
 
     float X[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f};
     float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -239,7 +235,6 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
 __global__ void k_residual(int64_t count, const float4* __restrict__ image, const float4* __restrict__ target,
                            float4* __restrict__ d_image, int64_t count4) {
     pdl_wait();
-    pdl_trigger();
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count4; j += (int64_t)gridDim.x * blockDim.x) {
         const float4 a = __ldg(image + j), b = __ldg(target + j);
         d_image[j] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);

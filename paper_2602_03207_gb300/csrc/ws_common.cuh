@@ -218,14 +218,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch. Every kernel of the path is launched with
-// programmatic stream serialisation, so it may be scheduled while its
-// predecessor in the stream drains; it calls pdl_wait() before its first
+// programmatic stream serialisation and calls pdl_wait() before its first
 // global-memory access (read or write), which returns once the predecessor
-// grid has completed and its writes are visible, and pdl_trigger() to let its
-// own successor launch early. Launch latency overlaps the predecessor's tail;
-// ordering and results are those of plain stream order.
+// grid has completed and its writes are visible. No kernel triggers its
+// dependents early (griddepcontrol.launch_dependents): a successor launches
+// as its predecessor's blocks exit, with the launch itself already prepared,
+// which measured faster than an early trigger (whose waiting blocks occupy
+// the SMs) and than no programmatic launch. Ordering and results are those
+// of plain stream order.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,

@@ -32,7 +32,6 @@ __global__ void __launch_bounds__(kScanThreads)
 k_chunk_sums(int64_t n, const uint32_t* __restrict__ touched, uint32_t* __restrict__ sums) {
     __shared__ uint32_t s_red[kScanThreads / 32 + 1];
     pdl_wait();
-    pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * kChunk;
     uint32_t acc = 0;
 #pragma unroll
@@ -52,7 +51,6 @@ k_chunk_scan(int64_t nchunks, int64_t n, uint32_t* __restrict__ sums, uint32_t* 
              uint32_t* __restrict__ num_keys, int64_t capacity, uint32_t* __restrict__ status) {
     __shared__ uint32_t s_red[kTopThreads / 32 + 1];
     pdl_wait();
-    pdl_trigger();
     uint32_t carry = 0;
     for (int64_t start = 0; start < nchunks; start += kTopThreads) {
         int64_t c = start + threadIdx.x;
@@ -88,7 +86,6 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
     __shared__ uint32_t s_red[kScanThreads / 32 + 1];
     __shared__ __align__(16) uint16_t s_owner[kSlotCap];  // slot -> local Gaussian (fast path; < kChunk)
     pdl_wait();
-    pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * kChunk;
     const int cnt = (int)((n - base) < kChunk ? (n - base) : kChunk);
 

@@ -113,7 +113,6 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
     const bool valid = i < n;
     const int64_t warp_first = (int64_t)blockIdx.x * kPreThreads + warp * kWarp;
     pdl_wait();
-    pdl_trigger();
 
     float logit = 0.f, x = 0.f, y = 0.f, z = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -211,7 +210,6 @@ k_blend_packed(const uint2* __restrict__ ranges, const uint32_t* __restrict__ va
                const uint32_t* __restrict__ rgba, const Frame f, float* __restrict__ image,
                float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
     pdl_wait();
-    pdl_trigger();
     const PackedSplats sp{mean2d, axes, rgba};
     blend_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, sp, image, t_final, n_contrib);
 }

@@ -33,7 +33,6 @@ k_preprocess(int64_t n, const float* __restrict__ means, const float* __restrict
     const bool valid = i < n;
     const int64_t warp_first = (int64_t)blockIdx.x * kPreThreads + warp * kWarp;
     pdl_wait();
-    pdl_trigger();
 
     // All per-Gaussian inputs but the SH are requested at once.
     float logit = 0.f, x = 0.f, y = 0.f, z = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f;

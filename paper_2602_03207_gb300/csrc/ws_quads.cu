@@ -45,7 +45,6 @@ k_quad_setup(int64_t n, const float* __restrict__ conic, const float* __restrict
              const uint32_t* __restrict__ tiles_touched, const Frame f, QuadRec* __restrict__ quad,
              uint32_t* __restrict__ one, uint2* __restrict__ rect0) {
     pdl_wait();
-    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * kQuadThreads + threadIdx.x;
     if (i >= n) return;
     const bool vis = __ldg(tiles_touched + i) > 0u;
@@ -96,7 +95,6 @@ k_quad_bin_items(int64_t n, const uint32_t* __restrict__ num_vis, const uint32_t
                  const float4* __restrict__ mean2d, const QuadRec* __restrict__ quad, const Frame f,
                  uint32_t* __restrict__ touched, uint2* __restrict__ rect, float* __restrict__ zero_depth) {
     pdl_wait();
-    pdl_trigger();
     const int64_t k = (int64_t)blockIdx.x * kQuadThreads + threadIdx.x;
     if (k >= n) return;
     zero_depth[k] = 0.f;
@@ -146,7 +144,6 @@ k_blend_quads(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ran
     __shared__ QuadStage s_q[kQuadBatch];
     __shared__ uint32_t s_mask[kQuadBatch];
     pdl_wait();
-    pdl_trigger();
     const int tile = blockIdx.x;
     const uint2 range = ranges[tile];
     const int tx = tile % f.TX, ty = tile / f.TX;

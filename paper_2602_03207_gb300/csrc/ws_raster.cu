@@ -31,9 +31,7 @@ constexpr int kRangeThreads = 256;
 // (an empty tile gets start = end), in one pass over positions 0..n: at
 // position i, between the tiles a of key i-1 and c of key i, tiles a+1..c
 // start and tiles a..c-1 end (scan_boundaries). Keys whose tile is >= ntiles
-// (none in a frame) count as past the end. The blend is allowed to launch
-// only once this scan is done (the trigger is at the end): its blocks do not
-// wait on the SMs while the scan runs.
+// (none in a frame) count as past the end.
 __global__ void __launch_bounds__(kRangeThreads)
 k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys,
               uint2* __restrict__ ranges, uint32_t ntiles) {
@@ -48,7 +46,6 @@ k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ nu
                 if (t > lo && t < nt) ranges[t].x = pos;
             }
         });
-    pdl_trigger();
 }
 
 template <int TS>
@@ -58,7 +55,6 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
         const float* __restrict__ opacity, const float* __restrict__ rgb, const Frame f,
         float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
     pdl_wait();
-    pdl_trigger();
     const FloatSplats sp{mean2d, conic, opacity, rgb};
     blend_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, sp, image, t_final, n_contrib);
 }

@@ -51,7 +51,6 @@ k_sort_upsweep(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_hist[0][0])[d] = 0;
     pdl_wait();
-    pdl_trigger();
     const uint32_t n = *num_keys;
     const int tile = blockIdx.x;
     if ((int64_t)tile * kSortTile >= (int64_t)n) return;
@@ -87,7 +86,6 @@ k_sort_scan(const uint32_t* __restrict__ num_keys, uint32_t* __restrict__ hist,
             uint32_t* __restrict__ totals, int max_tiles) {
     __shared__ uint32_t s_red[kSortThreads / 32 + 1];
     pdl_wait();
-    pdl_trigger();
     const uint32_t n = *num_keys;
     const int tiles = (int)((n + kSortTile - 1) / kSortTile);
     uint32_t* row = hist + (size_t)blockIdx.x * max_tiles;
@@ -135,7 +133,6 @@ k_sort_downsweep(const uint64_t* __restrict__ keys_in, const uint32_t* __restric
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_wh[0][0])[d] = 0;
     pdl_wait();
-    pdl_trigger();
     const uint32_t n = *num_keys;
     const int tile = blockIdx.x;
     const int64_t tile_base = (int64_t)tile * kSortTile;

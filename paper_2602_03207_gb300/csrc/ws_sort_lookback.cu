@@ -70,7 +70,6 @@ k_lb_hist(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_ke
     extern __shared__ __align__(16) uint32_t s_h[];  // [passes][R]
     for (int e = threadIdx.x; e < passes * R; e += kLbThreads) s_h[e] = 0;
     pdl_wait();
-    pdl_trigger();
     if (blockIdx.x == 0 && threadIdx.x == 0) flags[1] = 0u;  // this sort's timeout word
     const int64_t gstride = (int64_t)gridDim.x * kLbThreads;
     for (int64_t e = (int64_t)blockIdx.x * kLbThreads + threadIdx.x; e < status_words; e += gstride) status0[e] = 0;
@@ -103,7 +102,6 @@ k_lb_hist_scan(const uint32_t* __restrict__ partials, int passes, uint32_t* __re
     constexpr int T = R > 256 ? R : 256;
     __shared__ uint32_t s_red[T / 32 + 1];
     pdl_wait();
-    pdl_trigger();
     const int p = blockIdx.x, d = threadIdx.x;
     uint32_t tot = 0;
     if (d < R)

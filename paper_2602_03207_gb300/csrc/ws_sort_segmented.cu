@@ -39,7 +39,6 @@ constexpr int kMaxSegBits = 24;
 
 // start[s] for s in (seg(i-1), seg(i)]: the first position of every segment,
 // empty ones included; start[nseg] = n (scan_boundaries over positions 0..n).
-// The local sorts are allowed to launch only once this scan is done.
 __global__ void __launch_bounds__(256)
 k_seg_bounds(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, uint32_t seg_mask,
              uint32_t nseg, uint32_t* __restrict__ start) {
@@ -51,7 +50,6 @@ k_seg_bounds(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num
         [&](int64_t lo, int64_t hi, uint32_t pos) {
             for (int64_t s = lo + 1 + lane; s <= hi; s += kWarp) start[s] = pos;
         });
-    pdl_trigger();
 }
 
 __device__ __forceinline__ uint32_t sub_key(uint64_t k, int begin_bit, uint32_t sub_mask) {
@@ -421,7 +419,6 @@ k_seg_sort(uint64_t* kin, uint32_t* vin, uint64_t* kout, uint32_t* vout, const u
     __shared__ uint32_t s_red[2 * kSegWarps + 2];
     const int warp = threadIdx.x >> 5;
     pdl_wait();
-    pdl_trigger();
     const uint32_t n_all = *num_keys;
     // segment s as [b, e), clamped into [0, n]
     auto bounds = [&](uint32_t s, uint32_t& b, uint32_t& e) {
