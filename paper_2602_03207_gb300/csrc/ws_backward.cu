@@ -49,7 +49,7 @@ k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
 
 constexpr int kPbThreads = 128;
 
-__global__ void __launch_bounds__(kPbThreads)
+__global__ void __launch_bounds__(kPbThreads, 8)
 k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __restrict__ log_scales,
                  const float4* __restrict__ quats, const float4* __restrict__ sh, const Frame f,
                  const float* __restrict__ rgb, const float* __restrict__ opacity,
@@ -118,10 +118,9 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
     }
     float* mine = stage + lane * kShPad;
     if (vis) {
-        float gsh[48];
-        sh_adjoint(f, X, mine, col, pr, gm, gsh, false);
-#pragma unroll
-        for (int k = 0; k < 48; ++k) mine[k] = gsh[k];
+        // the SH gradients overwrite this lane's staged coefficients in place
+        // (sh_adjoint reads every coefficient before it writes a gradient)
+        sh_adjoint(f, X, mine, col, pr, gm, mine, false);
     } else if (need) {
 #pragma unroll
         for (int k = 0; k < 48; ++k) mine[k] = 0.f;
