@@ -12,7 +12,7 @@ import pytest
 import oracle
 from paper_2602_03207_gb300 import synthetic as S
 
-from helpers import IMAGE_ATOL, compare_image, fetch, gpu_frame, last_gid
+from helpers import IMAGE_ATOL, capi_camera, compare_image, fetch, gpu_frame, last_gid
 
 pytestmark = pytest.mark.gpu
 
@@ -125,6 +125,30 @@ def test_ragged_resolution_and_background():
     _check_sort(g)
     st = compare_image(g, ref)
     assert st["n_bad"] == 0, st
+
+
+def test_culled_entries_are_written_as_zeros():
+    """Every output entry is written: a culled Gaussian's mean2d, conic, rgb,
+    opacity and rect are zeros, whatever the buffers held before."""
+    import torch
+    from paper_2602_03207_gb300 import render
+    scene, cam = S.small_forward()
+    n = scene["means"].shape[0]
+    r = render.Renderer(n, cam["width"], cam["height"])
+    for t in (r.mean2d, r.conic, r.rgb, r.opacity):
+        t.fill_(float("nan"))
+    r.rect.fill_(-1)
+    r.preprocess(render.scene_to_device(scene), capi_camera(cam))
+    torch.cuda.synchronize()
+    g = {"mean2d4": r.mean2d[:n].cpu().numpy(), "conic": r.conic[:n].cpu().numpy(),
+         "rgb": r.rgb[:n].cpu().numpy(), "opacity": r.opacity[:n].cpu().numpy(),
+         "rect": r.rect[:n].cpu().numpy().view(np.uint16),
+         "touched": r.tiles_touched[:n].cpu().numpy().view(np.uint32)}
+    culled = g["touched"] == 0
+    assert 0 < culled.sum() < n
+    for k in ("mean2d4", "conic", "rgb", "opacity", "rect"):
+        np.testing.assert_array_equal(g[k][culled], 0)
+        assert np.isfinite(g[k][~culled].astype(np.float64)).all(), k
 
 
 def test_empty_and_fully_culled_scenes():
