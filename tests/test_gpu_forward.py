@@ -133,6 +133,9 @@ def test_culled_entries_are_written_as_zeros():
     import torch
     from paper_2602_03207_gb300 import render
     scene, cam = S.small_forward()
+    scene = dict(scene)
+    scene["opacity_logits"] = scene["opacity_logits"].copy()
+    scene["opacity_logits"][::3] = -7.0  # below 1/255: culled
     n = scene["means"].shape[0]
     r = render.Renderer(n, cam["width"], cam["height"])
     for t in (r.mean2d, r.conic, r.rgb, r.opacity):
