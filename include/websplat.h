@@ -338,8 +338,9 @@ ws_status ws_rasterize_backward(int64_t n, const float *means, const float *log_
  * conic[V][n][3], depth[V][n], rgb[V][n][3], rect[V][n][4],
  * tiles_touched[V][n], offsets[V * n + 1]); opacity[n] is shared by all
  * views (0 for a Gaussian visible in none). Every entry is written, with
- * zeros for a (view, Gaussian) that is culled, as in ws_preprocess. Tiles are numbered in one global grid: view v's tiles follow those
- * of views 0..v-1, and the keys carry that global tile id (sort bits [0, 31 +
+ * zeros for a (view, Gaussian) that is culled, as in ws_preprocess. Tiles
+ * are numbered in one global grid: view v's tiles follow those of views
+ * 0..v-1, and the keys carry that global tile id (sort bits [0, 31 +
  * ceil(log2 total tiles))). Images are packed: view v's H_v x W_v x 3 floats
  * start after those of views 0..v-1 (likewise t_final and n_contrib).
  * ranges has one [start, end) pair per global tile. The paper renders one
