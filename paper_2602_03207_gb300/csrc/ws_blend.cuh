@@ -54,10 +54,11 @@ struct FloatSplats {
 
 // One block per tile. Each warp owns WPB (TS^2/256, at least 1) 8x4 pixel
 // blocks. Splats are staged 256 at a time; while staging, every splat also
-// records the bitmask of the tile's 8x4 blocks that its opacity-aware
-// ellipse reaches (splat_block_mask). Each warp then walks the batch 32 splats at a time,
-// ballots the bit of its own block and visits only those splats, in list
-// order, so per pixel the compositing order is unchanged.
+// records the bitmask of the tile's 8x4 blocks that the bounding box of its
+// opacity-aware ellipse meets (splat_block_mask). Each warp then walks the
+// batch 32 splats at a time, ballots the bit of its own block and visits
+// only those splats, in list order, so per pixel the compositing order is
+// unchanged.
 template <int TS, typename Splats>
 __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
                                            const Splats& sp, float* __restrict__ image, float* __restrict__ t_final,
