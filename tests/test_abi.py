@@ -119,3 +119,18 @@ def test_null_device_pointers_are_rejected(lib):
             else:
                 args.append(None)
         assert fn(*args) == capi.WS_ERR_INVALID_ARG, nm
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's flag and status constants equal the header's
+    #defines and enum values."""
+    from paper_2602_03207_gb300 import capi
+    src = open(os.path.join(ROOT, "include", "websplat.h")).read()
+    defines = {m.group(1): int(m.group(2), 0)
+               for m in re.finditer(r"#define\s+(WS_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+|\d+)u?\b", src)}
+    checked = 0
+    for name, value in defines.items():
+        if hasattr(capi, name):
+            assert getattr(capi, name) == value, name
+            checked += 1
+    assert checked >= 5, sorted(defines)
