@@ -101,6 +101,65 @@ def test_sh_cartesian_form_matches_definition_and_gradient():
             np.testing.assert_allclose(g[:, a], fd, atol=1e-8)
 
 
+def _odd_band_terms(d):
+    """A few real SH functions with the Condon-Shortley phase, typed from the
+    textbook Cartesian table (not from the oracle): l = 1, m = +1 and -1;
+    l = 3, m = -3, 0, +3. Index l^2 + l + m."""
+    x, y, z = d
+    k1 = math.sqrt(3 / (4 * math.pi))
+    k33 = math.sqrt(35 / (32 * math.pi))
+    k30 = math.sqrt(7 / (16 * math.pi))
+    return {3: -k1 * x, 1: -k1 * y,
+            9: -k33 * y * (3 * x * x - y * y), 12: k30 * z * (2 * z * z - 3 * x * x - 3 * y * y),
+            15: -k33 * x * (x * x - 3 * y * y)}
+
+
+def test_sh_colour_uses_direction_from_camera_centre():
+    """§2.1 colours a splat with SH(k, d), d the unit vector from the camera
+    centre to the splat's mean. The eye position is taken from the test (not
+    from the view matrix) and the colour is compared with 1/2 + sum k Y(d) for
+    splats behind, in front of and beside the look-at target, with only odd-band
+    coefficients set. A wrong camera centre (e.g. t instead of -R^T t) or a
+    reversed d (which negates every odd band) moves each channel by far more
+    than the tolerance; the test also checks that on its own expected values."""
+    rng = np.random.default_rng(21)
+    eyes = [(6.0, -4.0, 3.0), (-5.0, 7.0, -2.0), (0.5, -8.0, 6.0)]
+    target = np.array([0.3, -0.2, 0.4])
+    # channel 0: l=1 m=+1; channel 1: l=3 m=-3 and l=1 m=-1; channel 2: l=3 m=0 and m=+3
+    chan_terms = {0: (3,), 1: (9, 1), 2: (12, 15)}
+    for eye in eyes:
+        eye = np.array(eye)
+        cam = S.look_at_camera(eye, target, 96, 96, fov_x_deg=50.0)
+        fwd = (target - eye) / np.linalg.norm(target - eye)
+        right = np.cross(fwd, [0.0, 0.0, 1.0])
+        right /= np.linalg.norm(right)
+        means = np.stack([target + 0.6 * fwd, target - 0.6 * fwd, target + 0.6 * right,
+                          target - 0.4 * right + 0.3 * fwd])
+        n = means.shape[0]
+        sh = np.zeros((n, 16, 3))
+        for ch, idx in chan_terms.items():
+            for k in idx:
+                # |sum| < 1/2, so no channel reaches the clamp at 0
+                sh[:, k, ch] = rng.uniform(0.2, 0.45, n) * rng.choice([-1.0, 1.0], n)
+        p = oracle.preprocess(_scene(n, means, np.full((n, 3), -4.0), sh=sh), cam)
+        assert list(p["reason"]) == [0] * n
+        for i in range(n):
+            d = means[i] - eye
+            d /= np.linalg.norm(d)
+            Y, Yrev = _odd_band_terms(d), _odd_band_terms(-d)
+            wrong = means[i] - cam["viewmat"][:, 3].astype(float)  # t_v mistaken for the centre
+            Ybad = _odd_band_terms(wrong / np.linalg.norm(wrong))
+            for ch, idx in chan_terms.items():
+                s = sum(sh[i, k, ch] * Y[k] for k in idx)
+                expect = max(0.0, 0.5 + s)
+                assert abs(p["rgb"][i, ch] - expect) < 1e-6, (eye, i, ch)
+                # the pin is discriminating: the mistaken directions give other colours
+                rev = max(0.0, 0.5 + sum(sh[i, k, ch] * Yrev[k] for k in idx))
+                bad = max(0.0, 0.5 + sum(sh[i, k, ch] * Ybad[k] for k in idx))
+                assert abs(rev - expect) > 1e-3 or abs(s) < 1e-3
+                assert abs(bad - expect) > 1e-4 or abs(s) < 1e-3
+
+
 # -------------------------------------------------------- preprocess (§3.2)
 
 def test_isotropic_on_axis_closed_form():
