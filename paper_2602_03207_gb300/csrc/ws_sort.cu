@@ -45,13 +45,13 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // keys per block
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_upsweep(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, int shift,
-               uint32_t mask, uint32_t* __restrict__ hist, int max_tiles) {
+               uint32_t mask, uint32_t* __restrict__ hist, int max_tiles, uint32_t cap) {
     constexpr int R = 1 << BITS;
     __shared__ uint16_t s_hist[kSortWarps][R];  // per-warp counts (<= 512 each)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_hist[0][0])[d] = 0;
     pdl_wait();
-    const uint32_t n = *num_keys;
+    const uint32_t n = min(*num_keys, cap);
     const int tile = blockIdx.x;
     if ((int64_t)tile * kSortTile >= (int64_t)n) return;
     __syncthreads();
@@ -83,10 +83,10 @@ k_sort_upsweep(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n
 // total into totals[d].
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_scan(const uint32_t* __restrict__ num_keys, uint32_t* __restrict__ hist,
-            uint32_t* __restrict__ totals, int max_tiles) {
+            uint32_t* __restrict__ totals, int max_tiles, uint32_t cap) {
     __shared__ uint32_t s_red[kSortThreads / 32 + 1];
     pdl_wait();
-    const uint32_t n = *num_keys;
+    const uint32_t n = min(*num_keys, cap);
     const int tiles = (int)((n + kSortTile - 1) / kSortTile);
     uint32_t* row = hist + (size_t)blockIdx.x * max_tiles;
     uint32_t carry = 0;
@@ -119,7 +119,7 @@ k_sort_downsweep(const uint64_t* __restrict__ keys_in, const uint32_t* __restric
                  uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                  const uint32_t* __restrict__ num_keys, int shift, uint32_t mask,
                  const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals,
-                 int max_tiles) {
+                 int max_tiles, uint32_t cap) {
     constexpr int R = 1 << BITS;
     constexpr int kPerThread = R > kSortThreads ? R / kSortThreads : 1;
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -133,7 +133,7 @@ k_sort_downsweep(const uint64_t* __restrict__ keys_in, const uint32_t* __restric
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kSortWarps * R; d += kSortThreads) (&s_wh[0][0])[d] = 0;
     pdl_wait();
-    const uint32_t n = *num_keys;
+    const uint32_t n = min(*num_keys, cap);
     const int tile = blockIdx.x;
     const int64_t tile_base = (int64_t)tile * kSortTile;
     if (tile_base >= (int64_t)n) return;
@@ -259,6 +259,10 @@ cudaError_t sort_passes(const uint32_t* num_keys, int64_t capacity, int begin_bi
                         uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                         SortScratch s, int* in_alt, cudaStream_t stream) {
     const int max_tiles = max_tiles_for(capacity);
+    // A count above the capacity is clamped to it on the device (the caller
+    // states it must not exceed it), so no pass writes past the key buffers,
+    // the histogram rows or the totals.
+    const uint32_t cap = (uint32_t)capacity;
     constexpr size_t smem = downsweep_smem<BITS>();
     // The dynamic shared-memory limit is a per-device function attribute:
     // set it once per (instantiation, device).
@@ -282,14 +286,14 @@ cudaError_t sort_passes(const uint32_t* num_keys, int64_t capacity, int begin_bi
         const uint32_t mask = (1u << bits) - 1u;
         if (max_tiles > 0) {
             e = launch_pdl(k_sort_upsweep<BITS>, dim3(max_tiles), dim3(kSortThreads), 0, stream,
-                           (const uint64_t*)kin, num_keys, shift, mask, s.hist, max_tiles);
+                           (const uint64_t*)kin, num_keys, shift, mask, s.hist, max_tiles, cap);
             if (e != cudaSuccess) return e;
             e = launch_pdl(k_sort_scan, dim3(1 << BITS), dim3(kSortThreads), 0, stream, num_keys, s.hist,
-                           s.totals, max_tiles);
+                           s.totals, max_tiles, cap);
             if (e != cudaSuccess) return e;
             e = launch_pdl(k_sort_downsweep<BITS>, dim3(max_tiles), dim3(kSortThreads), smem, stream,
                            (const uint64_t*)kin, (const uint32_t*)vin, kout, vout, num_keys, shift, mask,
-                           (const uint32_t*)s.hist, (const uint32_t*)s.totals, max_tiles);
+                           (const uint32_t*)s.hist, (const uint32_t*)s.totals, max_tiles, cap);
             if (e != cudaSuccess) return e;
         }
         uint64_t* tk = kin; kin = kout; kout = tk;
@@ -352,6 +356,9 @@ constexpr int64_t kNoAllocMaxKeys = int64_t(1) << 23;  // 8,388,608 keys
 constexpr int kNoAllocMaxTiles = (int)((kNoAllocMaxKeys + kSortTile - 1) / kSortTile);
 constexpr int kNoAllocMaxDigits = 256;  // 8-bit digits at most
 constexpr size_t kNoAllocWords = (size_t)kNoAllocMaxDigits * kNoAllocMaxTiles + kNoAllocMaxDigits;
+// 4 MiB + 1 KiB with 2,048-key blocks (the figure the header states).
+static_assert(kNoAllocWords * sizeof(uint32_t) == (size_t(4) << 20) + 1024,
+              "the documented size of the allocation-free sort's scratch");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
@@ -359,7 +366,7 @@ uint32_t* g_noalloc_ptr[kMaxDevices] = {};
 
 }  // namespace
 
-// 2 MiB + 1 KiB per device: the digit-major histogram matrix for
+// 4 MiB + 1 KiB per device: the digit-major histogram matrix for
 // kNoAllocMaxKeys keys plus the digit totals.
 static __device__ __align__(256) uint32_t ws_sort_noalloc_scratch[kNoAllocWords];
 

@@ -65,7 +65,7 @@ template <int BITS>
 __global__ void __launch_bounds__(kLbThreads)
 k_lb_hist(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, int begin_bit, int passes,
           int end_bit, uint32_t* __restrict__ partials, uint64_t* __restrict__ status0, int64_t status_words,
-          uint32_t* __restrict__ flags) {
+          uint32_t* __restrict__ flags, uint32_t cap) {
     constexpr int R = 1 << BITS;
     extern __shared__ __align__(16) uint32_t s_h[];  // [passes][R]
     for (int e = threadIdx.x; e < passes * R; e += kLbThreads) s_h[e] = 0;
@@ -74,7 +74,7 @@ k_lb_hist(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_ke
     const int64_t gstride = (int64_t)gridDim.x * kLbThreads;
     for (int64_t e = (int64_t)blockIdx.x * kLbThreads + threadIdx.x; e < status_words; e += gstride) status0[e] = 0;
     __syncthreads();
-    const uint32_t n = *num_keys;
+    const uint32_t n = min(*num_keys, cap);
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * kLbThreads; base < n; base += gstride) {
         const int64_t i = base + threadIdx.x;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kLbThreads)
 k_lb_pass(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
           uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ num_keys,
           int shift, uint32_t mask, const uint32_t* __restrict__ base, uint64_t* __restrict__ st_cur,
-          uint64_t* __restrict__ st_next, uint32_t* __restrict__ flags, int drop_tile) {
+          uint64_t* __restrict__ st_next, uint32_t* __restrict__ flags, int drop_tile, uint32_t cap) {
     constexpr int R = 1 << BITS;
     constexpr int kPer = R > kLbThreads ? R / kLbThreads : 1;
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -130,7 +130,7 @@ k_lb_pass(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ val
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     pdl_wait();
-    const uint32_t n = *num_keys;
+    const uint32_t n = min(*num_keys, cap);
     const int tiles = (int)((n + kLbTile - 1) / kLbTile);
     const uint32_t lt = lanemask_lt();
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -315,7 +315,7 @@ cudaError_t lb_sort(const uint32_t* num_keys, int64_t cap, int begin_bit, int en
     const int grid = tiles < sms * occ ? tiles : sms * occ;
     e = launch_pdl(k_lb_hist<BITS>, dim3(kLbHistBlocks), dim3(kLbThreads), (size_t)passes * R * 4, stream,
                    (const uint64_t*)keys, num_keys, begin_bit, passes, end_bit, s.partials, s.st[0],
-                   (int64_t)tiles * R, flags);
+                   (int64_t)tiles * R, flags, (uint32_t)cap);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_lb_hist_scan<BITS>, dim3(passes), dim3(R > 256 ? R : 256), 0, stream,
                    (const uint32_t*)s.partials, passes, s.base);
@@ -332,7 +332,7 @@ cudaError_t lb_sort(const uint32_t* num_keys, int64_t cap, int begin_bit, int en
             e = launch_pdl(k_lb_pass<BITS>, dim3(grid), dim3(kLbThreads), smem, stream, (const uint64_t*)kin,
                            (const uint32_t*)vin, kout, vout, num_keys, shift, mask,
                            (const uint32_t*)(s.base + p * R), s.st[p & 1], s.st[(p + 1) & 1], flags,
-                           p == 0 ? drop_tile : -1);
+                           p == 0 ? drop_tile : -1, (uint32_t)cap);
             if (e != cudaSuccess) return e;
         }
         uint64_t* tk = kin; kin = kout; kout = tk;

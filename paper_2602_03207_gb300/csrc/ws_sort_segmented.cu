@@ -40,12 +40,12 @@ constexpr int kMaxSegBits = 24;
 // start[s] for s in (seg(i-1), seg(i)]: the first position of every segment,
 // empty ones included; start[nseg] = n (scan_boundaries over positions 0..n).
 __global__ void __launch_bounds__(256)
-k_seg_bounds(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, uint32_t seg_mask,
-             uint32_t nseg, uint32_t* __restrict__ start) {
+k_seg_bounds(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, uint32_t cap,
+             uint32_t seg_mask, uint32_t nseg, uint32_t* __restrict__ start) {
     pdl_wait();
     const int lane = threadIdx.x & 31;
     scan_boundaries<4>(
-        keys, *num_keys, (int64_t)nseg,
+        keys, min(*num_keys, cap), (int64_t)nseg,
         [seg_mask](uint64_t k) { return (int64_t)((uint32_t)(k >> kSplitBit) & seg_mask); },
         [&](int64_t lo, int64_t hi, uint32_t pos) {
             for (int64_t s = lo + 1 + lane; s <= hi; s += kWarp) start[s] = pos;
@@ -411,7 +411,7 @@ __device__ void block_sort_global(uint64_t* kin, uint32_t* vin, uint64_t* kout, 
 // in launch order so their longer sorts start early.
 __global__ void __launch_bounds__(kSegThreads, 4)
 k_seg_sort(uint64_t* kin, uint32_t* vin, uint64_t* kout, uint32_t* vout, const uint32_t* __restrict__ start,
-           const uint32_t* __restrict__ num_keys, uint32_t nseg, int begin_bit) {
+           const uint32_t* __restrict__ num_keys, uint32_t cap, uint32_t nseg, int begin_bit) {
     __shared__ __align__(16) uint64_t s_key[kCtaCap];
     __shared__ __align__(16) uint32_t s_val[kCtaCap];
     __shared__ uint32_t s_cnt[kSegWarps][kLocalRadix];
@@ -419,7 +419,7 @@ k_seg_sort(uint64_t* kin, uint32_t* vin, uint64_t* kout, uint32_t* vout, const u
     __shared__ uint32_t s_red[2 * kSegWarps + 2];
     const int warp = threadIdx.x >> 5;
     pdl_wait();
-    const uint32_t n_all = *num_keys;
+    const uint32_t n_all = min(*num_keys, cap);
     // segment s as [b, e), clamped into [0, n]
     auto bounds = [&](uint32_t s, uint32_t& b, uint32_t& e) {
         e = min(__ldg(start + s + 1), n_all);
@@ -502,10 +502,10 @@ cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t spans = (key_capacity + 1 + 1023) / 1024;
     e = launch_pdl(k_seg_bounds, dim3((unsigned)(spans < sms * 8 ? spans : sms * 8)), dim3(256), 0, stream,
-                   (const uint64_t*)pk, num_keys, nseg - 1u, nseg, start);
+                   (const uint64_t*)pk, num_keys, (uint32_t)key_capacity, nseg - 1u, nseg, start);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_seg_sort, dim3(nseg + (nseg + kSegWarps - 1) / kSegWarps), dim3(kSegThreads), 0, stream, pk, pv,
-                   ok, ov, (const uint32_t*)start, num_keys, nseg, begin_bit);
+                   ok, ov, (const uint32_t*)start, num_keys, (uint32_t)key_capacity, nseg, begin_bit);
     if (e != cudaSuccess) return e;
     *in_alt = !part_alt;
     return cudaGetLastError();

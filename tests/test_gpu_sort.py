@@ -237,3 +237,36 @@ def test_segmented_sort_of_standard_keys():
     ek, ev = oracle.sort_pairs(keys, vals)
     np.testing.assert_array_equal(k, ek)
     np.testing.assert_array_equal(v, ev)
+
+
+@pytest.mark.parametrize("flags", [0, SEG, 4], ids=["lsd", "segmented", "lookback"])
+def test_count_above_capacity_is_clamped(flags):
+    """A device-side count larger than key_capacity is clamped to it: the
+    first key_capacity pairs come out sorted, and nothing past key_capacity
+    in the four key/value buffers, nor past the workspace, is written."""
+    import torch
+    from paper_2602_03207_gb300 import capi
+    assert flags != 4 or capi.WS_CFG_SORT_LOOKBACK == 4
+    rng = np.random.default_rng(31 + flags)
+    cap, guard = 20_000, 4096
+    keys, vals = _tile_depth_keys([int(x) for x in rng.integers(24, 40, 1024)], rng)
+    keys, vals = keys[:cap + guard], vals[:cap + guard]
+    assert keys.size == cap + guard
+    kt = torch.from_numpy(keys.view(np.int64)).cuda()
+    vt = torch.from_numpy(vals.view(np.int32)).cuda()
+    ka = torch.full_like(kt, -5)
+    va = torch.full_like(vt, -7)
+    before = [t.clone() for t in (kt, vt, ka, va)]
+    num = torch.tensor([cap + 3000, 0, 0, 0], dtype=torch.int32, device="cuda")
+    cfg = capi.config(digit_bits=8, flags=flags)
+    wsb = capi.ws_workspace_bytes(0, cap, capi.camera(S.small_forward()[1]), cfg)
+    ws = torch.full((wsb + 4096,), 0xAB, dtype=torch.uint8, device="cuda")
+    in_alt = capi.ws_sort(num, cap, 0, 41, kt, vt, ka, va, cfg, ws)
+    torch.cuda.synchronize()
+    k, v = (ka, va) if in_alt else (kt, vt)
+    ek, ev = oracle.sort_pairs(keys[:cap], vals[:cap])
+    np.testing.assert_array_equal(k[:cap].cpu().numpy().view(np.uint64), ek)
+    np.testing.assert_array_equal(v[:cap].cpu().numpy().view(np.uint32), ev)
+    for t, b in zip((kt, vt, ka, va), before):
+        assert torch.equal(t[cap:], b[cap:])
+    assert bool((ws[wsb:] == 0xAB).all())

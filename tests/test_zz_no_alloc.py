@@ -72,3 +72,60 @@ def test_no_alloc_rejects_oversize_capacity():
     with pytest.raises(capi.WsError) as e:
         capi.ws_sort_noalloc(num, cap + 1, 0, 40, k, v, k, v)
     assert e.value.status == capi.WS_ERR_INVALID_ARG
+
+
+def test_no_alloc_at_the_maximum_capacity():
+    """key_capacity equal to ws_sort_noalloc_max_keys() with 8-bit digits:
+    the histogram matrix and the digit totals then fill the whole static
+    array. A count just below the capacity sorts like ws_sort."""
+    import torch
+    from paper_2602_03207_gb300 import capi
+    cap = capi.ws_sort_noalloc_max_keys()
+    n = cap - 1234
+    rng = np.random.default_rng(77)
+    keys = rng.integers(0, 2 ** 44, n, dtype=np.uint64)
+    vals = rng.permutation(n).astype(np.uint32)
+    ek, ev = _with_workspace(keys, vals, 44, 8)
+    kt, vt, ka, va, num = _buffers(keys, vals, cap)
+    alt = capi.ws_sort_noalloc(num, cap, 0, 44, kt, vt, ka, va, digit_bits=8)
+    torch.cuda.synchronize()
+    k, v = (ka, va) if alt else (kt, vt)
+    np.testing.assert_array_equal(k[:n].cpu().numpy(), ek)
+    np.testing.assert_array_equal(v[:n].cpu().numpy(), ev)
+
+
+def test_no_alloc_count_above_capacity_is_clamped():
+    """A device-side count above key_capacity sorts the first key_capacity
+    pairs and writes nothing past them."""
+    import torch
+    from paper_2602_03207_gb300 import capi
+    rng = np.random.default_rng(78)
+    cap, extra = 50_000, 4096
+    keys = rng.integers(0, 2 ** 40, cap + extra, dtype=np.uint64)
+    vals = np.arange(cap + extra, dtype=np.uint32)
+    kt = torch.from_numpy(keys.view(np.int64)).cuda()
+    vt = torch.from_numpy(vals.view(np.int32)).cuda()
+    ka, va = torch.full_like(kt, -1), torch.full_like(vt, -1)
+    before = [t.clone() for t in (kt, vt, ka, va)]
+    num = torch.tensor([cap + extra, 0, 0, 0], dtype=torch.int32, device="cuda")
+    alt = capi.ws_sort_noalloc(num, cap, 0, 40, kt, vt, ka, va, digit_bits=8)
+    torch.cuda.synchronize()
+    k, v = (ka, va) if alt else (kt, vt)
+    perm = np.argsort(keys[:cap], kind="stable")
+    np.testing.assert_array_equal(k[:cap].cpu().numpy().view(np.uint64), keys[:cap][perm])
+    np.testing.assert_array_equal(v[:cap].cpu().numpy().view(np.uint32), vals[:cap][perm])
+    for t, b in zip((kt, vt, ka, va), before):
+        assert torch.equal(t[cap:], b[cap:])
+
+
+def test_no_alloc_rejects_unsupported_digit_width():
+    """Digit widths outside 4..8 return WS_ERR_UNSUPPORTED before any launch."""
+    import torch
+    from paper_2602_03207_gb300 import capi
+    num = torch.zeros(4, dtype=torch.int32, device="cuda")
+    k = torch.zeros(4, dtype=torch.int64, device="cuda")
+    v = torch.zeros(4, dtype=torch.int32, device="cuda")
+    for bits in (3, 9, 11):
+        with pytest.raises(capi.WsError) as e:
+            capi.ws_sort_noalloc(num, 4, 0, 40, k, v, k, v, digit_bits=bits)
+        assert e.value.status == capi.WS_ERR_UNSUPPORTED
