@@ -366,7 +366,7 @@ ws_status ws_rasterize_backward(int64_t n, const float* means, const float* log_
     return cuda_status(ws::launch_backward(n, means, log_scales, quats, sh, f, mean2d, conic, rgb, opacity,
                                            rect, offsets, tiles_touched, vals, ranges, t_final, n_contrib,
                                            d_image, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
-                                           ws_base + layout(0, key_capacity).bwd,
+                                           key_capacity, ws_base + layout(0, key_capacity).bwd,
                                            static_cast<cudaStream_t>(stream)));
 }
 
@@ -459,7 +459,7 @@ ws_status ws_rasterize_backward_batch(int64_t n, const float* means, const float
     return cuda_status(ws::launch_backward_batch(n, means, log_scales, quats, sh, ft, mean2d, conic, rgb, opacity,
                                                  rect, offsets, tiles_touched, vals, ranges, t_final, n_contrib,
                                                  d_image, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
-                                                 ws_base + layout(0, key_capacity).bwd,
+                                                 key_capacity, ws_base + layout(0, key_capacity).bwd,
                                                  static_cast<cudaStream_t>(stream)));
 }
 

@@ -54,7 +54,7 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
                  const float4* __restrict__ quats, const float4* __restrict__ sh, const Frame f,
                  const float* __restrict__ rgb, const float* __restrict__ opacity,
                  const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ touched,
-                 const float* __restrict__ partials, float* __restrict__ d_means,
+                 uint32_t cap, const float* __restrict__ partials, float* __restrict__ d_means,
                  float* __restrict__ d_log_scales, float4* __restrict__ d_quats,
                  float* __restrict__ d_logits, float4* __restrict__ d_sh) {
     __shared__ __align__(16) float s_sh[kPbThreads / kWarp][kWarp * kShPad];
@@ -90,6 +90,9 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
     float col[3] = {0.f, 0.f, 0.f};
     if (vis) {
         const uint32_t first = __ldg(offsets + i);
+        // pairs at slots past the key capacity were dropped by the emission
+        // (the frame carries WS_FLAG_CAPACITY): their records do not exist
+        const uint32_t nrec = first >= cap ? 0u : min(cnt, cap - first);
         X[0] = __ldg(means + 3 * i);
         X[1] = __ldg(means + 3 * i + 1);
         X[2] = __ldg(means + 3 * i + 2);
@@ -101,7 +104,7 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
         col[2] = __ldg(rgb + 3 * i + 2);
         // slot-ordered sum of this Gaussian's pair records
         const float* src = partials + (size_t)first * kPart;
-        for (uint32_t s = 0; s < cnt; ++s)
+        for (uint32_t s = 0; s < nrec; ++s)
 #pragma unroll
             for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
         glogit = pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
@@ -170,7 +173,7 @@ cudaError_t launch_backward(int64_t n, const float* means, const float* log_scal
                             const uint32_t* vals, const uint32_t* ranges, const float* t_final,
                             const uint32_t* n_contrib, const float* d_image, float* d_means,
                             float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
-                            void* scratch, cudaStream_t stream) {
+                            int64_t key_capacity, void* scratch, cudaStream_t stream) {
     float* partials = static_cast<float*>(scratch);
     const int ntiles = f.TX * f.TY;
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
@@ -200,7 +203,7 @@ cudaError_t launch_backward(int64_t n, const float* means, const float* log_scal
         const int64_t blocks = (n + kPbThreads - 1) / kPbThreads;
         e = launch_pdl(k_preprocess_bwd, dim3((unsigned)blocks), dim3(kPbThreads), 0, stream, n, means, log_scales,
                        reinterpret_cast<const float4*>(quats), reinterpret_cast<const float4*>(sh), f, rgb, opacity,
-                       offsets, tiles_touched, (const float*)partials, d_means, d_log_scales,
+                       offsets, tiles_touched, (uint32_t)key_capacity, (const float*)partials, d_means, d_log_scales,
                        reinterpret_cast<float4*>(d_quats), d_logits, reinterpret_cast<float4*>(d_sh));
     }
     return e;

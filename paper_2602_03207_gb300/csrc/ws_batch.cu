@@ -141,7 +141,7 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
                        const float4* __restrict__ quats, const float4* __restrict__ sh, const FrameTable ft,
                        const float* __restrict__ rgb, const float* __restrict__ opacity,
                        const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ touched,
-                       const float* __restrict__ partials, float* __restrict__ d_means,
+                       uint32_t cap, const float* __restrict__ partials, float* __restrict__ d_means,
                        float* __restrict__ d_log_scales, float4* __restrict__ d_quats,
                        float* __restrict__ d_logits, float4* __restrict__ d_sh) {
     __shared__ __align__(16) float s_sh[kBatchThreads / kWarp][kWarp * kShPad];
@@ -200,8 +200,11 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
         float pr[kPart];
 #pragma unroll
         for (int c = 0; c < kPart; ++c) pr[c] = 0.f;
+        // records past the key capacity were never written (the emission
+        // dropped those pairs and raised WS_FLAG_CAPACITY)
+        const uint32_t nrec = first >= cap ? 0u : min(cnt, cap - first);
         const float* src = partials + (size_t)first * kPart;
-        for (uint32_t s = 0; s < cnt; ++s)
+        for (uint32_t s = 0; s < nrec; ++s)
 #pragma unroll
             for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
         glogit += pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
@@ -292,7 +295,8 @@ cudaError_t launch_backward_batch(int64_t n, const float* means, const float* lo
                                   const uint32_t* offsets, const uint32_t* tiles_touched, const uint32_t* vals,
                                   const uint32_t* ranges, const float* t_final, const uint32_t* n_contrib,
                                   const float* d_image, float* d_means, float* d_log_scales, float* d_quats,
-                                  float* d_logits, float* d_sh, void* scratch, cudaStream_t stream) {
+                                  float* d_logits, float* d_sh, int64_t key_capacity, void* scratch,
+                                  cudaStream_t stream) {
     float* partials = static_cast<float*>(scratch);
     const uint32_t ntiles = ft.tile_off[ft.views];
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
@@ -322,7 +326,8 @@ cudaError_t launch_backward_batch(int64_t n, const float* means, const float* lo
         const int64_t blocks = (n + kBatchThreads - 1) / kBatchThreads;
         e = launch_pdl(k_preprocess_bwd_batch, dim3((unsigned)blocks), dim3(kBatchThreads), 0, stream, n, means,
                        log_scales, reinterpret_cast<const float4*>(quats), reinterpret_cast<const float4*>(sh), ft, rgb,
-                       opacity, offsets, tiles_touched, (const float*)partials, d_means, d_log_scales,
+                       opacity, offsets, tiles_touched, (uint32_t)key_capacity, (const float*)partials, d_means,
+                       d_log_scales,
                        reinterpret_cast<float4*>(d_quats), d_logits, reinterpret_cast<float4*>(d_sh));
     }
     return e;

@@ -27,43 +27,81 @@ constexpr int kChunk = kScanThreads * kScanItems;  // Gaussians per block
 constexpr int kTopThreads = 1024;
 constexpr int kSlotCap = 4096;  // slots per chunk resolved through shared memory
 
+// Pair counts are summed in 64 bits and stored saturated at 2^32 - 1: a
+// frame may cover more than 2^32 pairs (screen-filling splats with the
+// culling switched off), and a saturated slot is past any key capacity
+// (< 2^31), so such pairs are dropped and the capacity flag is raised
+// instead of wrapping around onto valid slots.
+constexpr uint32_t kSlotSat = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t sat32(uint64_t v) { return v < (uint64_t)kSlotSat ? (uint32_t)v : kSlotSat; }
+
 // Level 0 up: one sum of tiles_touched per chunk.
 __global__ void __launch_bounds__(kScanThreads)
 k_chunk_sums(int64_t n, const uint32_t* __restrict__ touched, uint32_t* __restrict__ sums) {
-    __shared__ uint32_t s_red[kScanThreads / 32 + 1];
+    __shared__ uint64_t s_red[kScanThreads / 32];
     pdl_wait();
     const int64_t base = (int64_t)blockIdx.x * kChunk;
-    uint32_t acc = 0;
+    uint64_t acc = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         int64_t i = base + threadIdx.x + k * kScanThreads;
         if (i < n) acc += __ldg(touched + i);
     }
-    uint32_t total;
-    block_exclusive_scan<kScanThreads>(acc, s_red, &total);
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (lane == 0) s_red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+#pragma unroll
+        for (int w = 0; w < kScanThreads / 32; ++w) t += s_red[w];
+        sums[blockIdx.x] = sat32(t);
+    }
 }
 
-// Level 1: exclusive scan of the chunk sums in one block; total pairs,
-// the clamped key count and the capacity flag.
+// Level 1: exclusive scan of the chunk sums in one block (64-bit running
+// total, chunk offsets stored saturated); total pairs, the clamped key count
+// and the capacity flag.
 __global__ void __launch_bounds__(kTopThreads)
 k_chunk_scan(int64_t nchunks, int64_t n, uint32_t* __restrict__ sums, uint32_t* __restrict__ offsets,
              uint32_t* __restrict__ num_keys, int64_t capacity, uint32_t* __restrict__ status) {
-    __shared__ uint32_t s_red[kTopThreads / 32 + 1];
+    __shared__ uint64_t s_red[kTopThreads / 32 + 1];
     pdl_wait();
-    uint32_t carry = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t carry = 0;
     for (int64_t start = 0; start < nchunks; start += kTopThreads) {
-        int64_t c = start + threadIdx.x;
-        uint32_t v = c < nchunks ? sums[c] : 0u;
-        uint32_t total;
-        uint32_t ex = block_exclusive_scan<kTopThreads>(v, s_red, &total);
-        if (c < nchunks) sums[c] = carry + ex;
-        carry += total;
+        const int64_t c = start + threadIdx.x;
+        const uint64_t v = c < nchunks ? sums[c] : 0u;
+        uint64_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_red[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const uint64_t w = s_red[lane];
+            uint64_t s = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(kFull, s, o);
+                if (lane >= o) s += y;
+            }
+            s_red[lane] = s - w;
+            if (lane == 31) s_red[32] = s;
+        }
+        __syncthreads();
+        if (c < nchunks) sums[c] = sat32(carry + s_red[warp] + x - v);
+        carry += s_red[32];
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
-        offsets[n] = carry;
-        const bool over = (int64_t)carry > capacity;
-        *num_keys = over ? (uint32_t)capacity : carry;
+        offsets[n] = sat32(carry);
+        const bool over = carry > (uint64_t)capacity;
+        *num_keys = over ? (uint32_t)capacity : (uint32_t)carry;
         // This frame's status words: stored outright, so no clear is needed.
         status[0] = over ? 1u : 0u;
         status[1] = 0u;
@@ -101,12 +139,14 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
     }
     uint32_t total;
     uint32_t ex = block_exclusive_scan<kScanThreads>(acc, s_red, &total);
+    // A saturated chunk offset (2^32 - 1) puts every slot of the chunk past
+    // the capacity; offsets are stored saturated likewise.
     const uint32_t coff = chunk_off[blockIdx.x];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         int li = threadIdx.x * kScanItems + k;
         s_off[li] = ex;
-        if (li < cnt) offsets[base + li] = coff + ex;
+        if (li < cnt) offsets[base + li] = sat32((uint64_t)coff + ex);
         ex += v[k];
     }
     if (threadIdx.x == 0) s_off[kChunk] = total;
@@ -128,7 +168,10 @@ k_emit(int64_t n, const uint32_t* __restrict__ touched, const uint2* __restrict_
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int li = threadIdx.x * kScanItems + k;
-            if (li < cnt && v[k] > 0) s_owner[s_off[li]] = (uint16_t)li;
+            // (s_off[li] < total always holds unless the chunk's counts sum
+            // past 2^32 and wrap; such a frame is flagged, and the test keeps
+            // the store inside the array)
+            if (li < cnt && v[k] > 0 && s_off[li] < total) s_owner[s_off[li]] = (uint16_t)li;
         }
         __syncthreads();
         // running maximum over the slots: thread-serial over kSlotPer slots

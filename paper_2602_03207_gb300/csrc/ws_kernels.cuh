@@ -95,7 +95,7 @@ cudaError_t launch_backward(int64_t n, const float* means, const float* log_scal
                             const uint32_t* vals, const uint32_t* ranges, const float* t_final,
                             const uint32_t* n_contrib, const float* d_image, float* d_means,
                             float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
-                            void* scratch, cudaStream_t stream);
+                            int64_t key_capacity, void* scratch, cudaStream_t stream);
 
 // ---- batched views (view-major per-(view, Gaussian) arrays)
 cudaError_t launch_preprocess_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
@@ -112,7 +112,8 @@ cudaError_t launch_backward_batch(int64_t n, const float* means, const float* lo
                                   const uint32_t* offsets, const uint32_t* tiles_touched, const uint32_t* vals,
                                   const uint32_t* ranges, const float* t_final, const uint32_t* n_contrib,
                                   const float* d_image, float* d_means, float* d_log_scales, float* d_quats,
-                                  float* d_logits, float* d_sh, void* scratch, cudaStream_t stream);
+                                  float* d_logits, float* d_sh, int64_t key_capacity, void* scratch,
+                                  cudaStream_t stream);
 cudaError_t launch_residual(int64_t count, const float* image, const float* target, float* d_image,
                             cudaStream_t stream);
 
