@@ -145,8 +145,10 @@ ws_status ws_preprocess(int64_t n, const float *means, const float *log_scales,
  * (the depth is positive, so its sign bit is 0 and key order is (tile,
  * depth) order). num_keys (device, one uint32) receives min(total,
  * key_capacity); pairs past key_capacity are dropped and WS_FLAG_CAPACITY
- * is raised. Clears the workspace status word first. key_capacity must be
- * < 2^31. */
+ * is raised. The pair total is accumulated in 64 bits: a frame may cover
+ * more than 2^32 pairs, and offsets are then stored saturated at
+ * 2^32 - 1 (every such slot lies past the capacity). Clears the workspace
+ * status word first. key_capacity must be < 2^31. */
 ws_status ws_cull(int64_t n, const uint32_t *tiles_touched, const uint16_t *rect,
                   const float *depth, const ws_camera *cam, const ws_config *cfg,
                   uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t key_capacity,
@@ -160,6 +162,9 @@ ws_status ws_cull(int64_t n, const uint32_t *tiles_touched, const uint16_t *rect
  * another and there are no global atomics, so the result does not depend
  * on scheduling. The key count is read from num_keys (device) so the
  * launch needs no host synchronisation; key_capacity bounds the grids.
+ * *num_keys must not exceed key_capacity; a larger count is clamped to
+ * key_capacity on the device (the first key_capacity pairs are sorted and
+ * nothing past the buffers or the scratch is written).
  * keys_alt / vals_alt (device, key_capacity entries) are the ping-pong
  * buffers. *result_in_alt (host) is set to 1 when the sorted data ends in
  * the _alt buffers (odd pass count), else 0. begin_bit < end_bit <= 64. */
@@ -211,10 +216,12 @@ ws_status ws_sort_test_stalled_tile(const uint32_t *num_keys, int64_t key_capaci
  * loop that must not call cudaMalloc (which can synchronise the device).
  * The paper has no counterpart; it is the same sort as ws_sort, with the
  * histogram scratch held in a static device array inside the library
- * (2 MiB + 1 KiB, kept by every GPU that loads the library until the process
+ * (4 MiB + 1 KiB, kept by every GPU that loads the library until the process
  * exits). The caller still passes the keys, values and ping-pong buffers.
  * key_capacity must not exceed ws_sort_noalloc_max_keys() (8,388,608);
- * larger values return WS_ERR_INVALID_ARG. digit_bits: 4..8. Allocates
+ * larger values return WS_ERR_INVALID_ARG. digit_bits: 4..8; any other
+ * width returns WS_ERR_UNSUPPORTED. *num_keys must not exceed
+ * key_capacity; a larger count is clamped to it on the device. Allocates
  * nothing. The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream
  * capture. All calls on one device share the array: calls that overlap on
