@@ -277,7 +277,14 @@ class RenderFunction(torch.autograd.Function):
     """Differentiable frame: image = render(means, log_scales, quats,
     opacity_logits, sh). The renderer's buffers hold the frame's
     intermediates between forward and backward, so one renderer serves one
-    frame in flight at a time."""
+    frame in flight at a time.
+
+    Forward and backward only enqueue work on the current stream: nothing
+    synchronises the host, so a whole training step can be captured in a
+    CUDA graph. The capacity check is the caller's: renderer.check_status()
+    (which synchronises) after the step raises if the frame's pairs
+    overflowed the key capacity, in which case the step's image and
+    gradients are incomplete."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, opacity_logits, sh, renderer, cam_dict):
@@ -285,7 +292,6 @@ class RenderFunction(torch.autograd.Function):
                  "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
                  "sh": sh.contiguous()}
         img = renderer.forward(scene, cam_dict)
-        renderer.check_status()
         ctx.renderer, ctx.cam, ctx.scene = renderer, cam_dict, scene
         return img.clone()
 
@@ -297,6 +303,7 @@ class RenderFunction(torch.autograd.Function):
 
 def render_differentiable(params, renderer, cam_dict):
     """params: dict of leaf tensors (means, log_scales, quats,
-    opacity_logits, sh); returns the image with autograd attached."""
+    opacity_logits, sh); returns the image with autograd attached.
+    Asynchronous; check renderer.check_status() after the step."""
     return RenderFunction.apply(params["means"], params["log_scales"], params["quats"],
                                 params["opacity_logits"], params["sh"], renderer, cam_dict)
