@@ -78,17 +78,34 @@ class BatchRenderer:
     def sorted_vals(self):
         return self.vals_alt if self.sorted_in_alt else self.vals
 
-    def forward(self, scene, stream=None):
+    # ------------------------------------------------------------ stages
+    def preprocess(self, scene, stream=None):
         capi.ws_preprocess_batch(self.n, scene["means"], scene["log_scales"], scene["quats"],
                                  scene["opacity_logits"], scene["sh"], self.cams_arr, self.cfg, self.mean2d,
                                  self.conic, self.depth, self.rgb, self.opacity, self.rect, self.tiles_touched, stream)
+
+    def cull(self, stream=None):
         capi.ws_cull_batch(self.n, self.cams_arr, self.cfg, self.tiles_touched, self.rect, self.depth, self.offsets,
                            self.keys, self.vals, self.key_capacity, self.num_keys, self.workspace, stream)
+
+    def sort(self, stream=None):
         self.sorted_in_alt = capi.ws_sort(self.num_keys, self.key_capacity, 0, self.end_bit, self.keys, self.vals,
                                           self.keys_alt, self.vals_alt, self.cfg, self.workspace, stream)
+
+    def rasterize(self, stream=None):
         capi.ws_rasterize_batch(self.num_keys, self.sorted_keys, self.sorted_vals, self.n, self.mean2d, self.conic,
                                 self.opacity, self.rgb, self.cams_arr, self.cfg, self.ranges, self.image,
                                 self.t_final, self.n_contrib, stream)
+
+    def residual(self, target, stream=None):
+        """d_image = image - target (gradient of 1/2 ||image - target||^2)."""
+        capi.ws_image_residual(self.total_pix * 3, self.image, target, self.d_image, stream)
+
+    def forward(self, scene, stream=None):
+        self.preprocess(scene, stream)
+        self.cull(stream)
+        self.sort(stream)
+        self.rasterize(stream)
         return self.image
 
     def backward(self, scene, d_image, stream=None):
@@ -104,7 +121,7 @@ class BatchRenderer:
     def step(self, scene, target, stream=None):
         """Forward, d_image = image - target (gradient of 1/2 ||image - target||^2), backward."""
         self.forward(scene, stream)
-        capi.ws_image_residual(self.total_pix * 3, self.image, target, self.d_image, stream)
+        self.residual(target, stream)
         return self.backward(scene, self.d_image, stream)
 
     def images(self):
