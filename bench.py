@@ -896,7 +896,7 @@ def batch_block(args, dev, min_timed_s=1.0, plain_min_s=0.5):
         lo, hi = np.searchsorted(gt, [b.tile_off[v], b.tile_off[v + 1]])
         a0, a1 = v * n, (v + 1) * n
         f = {"mean2d": (b.mean2d[a0:a1, :2].double() + b.mean2d[a0:a1, 2:].double()).cpu().numpy(),
-             "conic": b.conic[a0:a1].cpu().numpy(), "opacity": b.opacity[:n].cpu().numpy(),
+             "conic": b.conic[a0:a1].cpu().numpy(), "opacity": b.opacity[a0:a1].cpu().numpy(),
              "sorted_keys": ((gt[lo:hi] - b.tile_off[v]).astype(np.uint64) << np.uint64(31)),
              "sorted_vals": sv[lo:hi]}
         evals += blend_work(f, c["width"], c["height"], b.tile)

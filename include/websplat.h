@@ -31,6 +31,18 @@
  *   non-zero norm; opacity_logits[n]; sh[n][16][3] degree-3 spherical
  *   harmonic coefficients, coefficient-major (index l*l + l + m, real SH
  *   with the Condon-Shortley phase, i.e. the 3DGS PLY convention).
+ *
+ * Splat record (written by ws_preprocess, read by the blends): per Gaussian
+ * WS_SPLAT_FLOATS = 12 float32, 48 bytes, so one gather of a splat touches
+ * two 32-byte memory sectors:
+ *   [0] x_hi [1] y_hi [2] x_lo [3] y_lo  projected centre as the unevaluated
+ *        double-float sum (x_hi + x_lo, y_hi + y_lo) in pixels; x_hi alone
+ *        is the float32-rounded centre
+ *   [4] a [5] b [6] c                    conic Sigma'^{-1} = [[a, b], [b, c]]
+ *   [7] sigma                            opacity
+ *   [8] r [9] g [10] b                   colour
+ *   [11] 0
+ * A culled Gaussian's record is all zeros.
  */
 #ifndef WEBSPLAT_H
 #define WEBSPLAT_H
@@ -50,11 +62,13 @@ typedef int32_t ws_status;
 #define WS_ERR_TIMEOUT 4
 #define WS_ERR_UNSUPPORTED 5
 
-#define WS_ABI_VERSION 1
+#define WS_ABI_VERSION 2
 
 /* Status bits written to the device status word. */
 #define WS_FLAG_CAPACITY 1u /* more (tile, splat) pairs than key_capacity */
 #define WS_FLAG_TIMEOUT 2u  /* a bounded wait ran out (look-back sort only) */
+
+#define WS_SPLAT_FLOATS 12 /* floats per splat record (see the layout above) */
 
 /* Pinhole camera (§3.2 projects each centre and covariance to the image).
  * viewmat: row-major 3x4 [R | t] world -> camera, OpenCV axes (x right,
@@ -115,20 +129,15 @@ size_t ws_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera *cam,
  *   rgb = max(0, sum_lm sh_lm Y_lm(d) + 1/2), d = normalise(X - camera).
  * Inputs: the Gaussian arrays (device, layouts above).
  * Outputs (device, caller-allocated, n entries each):
- *   mean2d[n][4]  projected centre as the unevaluated double-float sum
- *                 (x_hi + x_lo, y_hi + y_lo), stored (x_hi, y_hi, x_lo, y_lo);
- *                 x_hi alone is the float32-rounded centre
- *   conic[n][3]   (a, b, c) of Sigma'^{-1} = [[a, b], [b, c]]
+ *   splats[n][12] the splat record above (centre, conic, sigma, colour)
  *   depth[n]      float32 view depth (written for every Gaussian)
- *   rgb[n][3], opacity[n] (sigma)
  *   rect[n][4]    uint16 tile rectangle x0, y0, x1, y1 (inclusive)
  *   tiles_touched[n]  uint32 tiles in rect; 0 means culled
  * Every entry is written; a culled Gaussian gets tiles_touched = 0 and
- * zeros in mean2d, conic, rgb, opacity and rect. */
+ * zeros in its splat record and rect. */
 ws_status ws_preprocess(int64_t n, const float *means, const float *log_scales,
                         const float *quats, const float *opacity_logits, const float *sh,
-                        const ws_camera *cam, const ws_config *cfg,
-                        float *mean2d, float *conic, float *depth, float *rgb, float *opacity,
+                        const ws_camera *cam, const ws_config *cfg, float *splats, float *depth,
                         uint16_t *rect, uint32_t *tiles_touched, void *stream);
 
 /* Compaction of the surviving splats into the <tile, splat> pair list
@@ -238,15 +247,14 @@ ws_status ws_sort_noalloc(const uint32_t *num_keys, int64_t key_capacity, int32_
  *   a = min(0.99, sigma exp(-q/2)), q = d^T conic d, d = pixel centre -
  *   centre; pairs with a < 1/255 are skipped; C += rgb a T; T *= 1 - a;
  *   image = C + T bg.
- * Inputs: num_keys (device), sorted keys and vals (device), the
- * ws_preprocess outputs. Outputs (device): ranges[tiles][2] uint32 [start,
+ * Inputs: num_keys (device), sorted keys and vals (device), the splat
+ * records of ws_preprocess. Outputs (device): ranges[tiles][2] uint32 [start,
  * end) of every tile in the sorted list (start = end for a tile without
  * pairs); image[H][W][3]; t_final[H][W]
  * (final transmittance); n_contrib[H][W] (1 + list position, relative to
  * the tile's start, of the last splat composited; 0 if none). */
 ws_status ws_rasterize(const uint32_t *num_keys, const uint64_t *keys, const uint32_t *vals,
-                       const float *mean2d, const float *conic, const float *opacity,
-                       const float *rgb, const ws_camera *cam, const ws_config *cfg,
+                       const float *splats, const ws_camera *cam, const ws_config *cfg,
                        uint32_t *ranges, float *image, float *t_final, uint32_t *n_contrib,
                        void *stream);
 
@@ -292,8 +300,8 @@ ws_status ws_rasterize_packed(const uint32_t *num_keys, const uint64_t *keys, co
  * the background. A fragment is a pixel centre with |p_x|, |p_y| <= r;
  * a = min(0.99, sigma e^{-p.p}) and fragments with a < 1/255 are skipped, so
  * the image equals ws_rasterize's within float rounding.
- * Inputs (device): the ws_preprocess outputs (mean2d, conic, opacity, rgb,
- * depth, tiles_touched). keys / vals / keys_alt / vals_alt (device,
+ * Inputs (device): the ws_preprocess outputs (splats, depth,
+ * tiles_touched). keys / vals / keys_alt / vals_alt (device,
  * key_capacity entries) hold the (tile, rank) pairs of the binning;
  * num_keys[0] (device) receives their count (WS_FLAG_CAPACITY in the
  * workspace status word when it exceeds key_capacity). Outputs (device):
@@ -301,8 +309,8 @@ ws_status ws_rasterize_packed(const uint32_t *num_keys, const uint64_t *keys, co
  * key_capacity, cam, cfg) bytes, 16-byte aligned; status read with
  * ws_read_status. Errors as ws_rasterize. */
 size_t ws_quads_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera *cam, const ws_config *cfg);
-ws_status ws_render_quads(int64_t n, const float *mean2d, const float *conic, const float *opacity,
-                          const float *rgb, const float *depth, const uint32_t *tiles_touched, const ws_camera *cam,
+ws_status ws_render_quads(int64_t n, const float *splats, const float *depth, const uint32_t *tiles_touched,
+                          const ws_camera *cam,
                           const ws_config *cfg, int64_t key_capacity, uint64_t *keys, uint32_t *vals,
                           uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *num_keys, float *image, float *t_final,
                           void *workspace, void *stream);
@@ -324,11 +332,10 @@ ws_status ws_render_quads(int64_t n, const float *mean2d, const float *conic, co
  * outputs, offsets (ws_cull), the sorted vals (ws_sort), ranges, t_final and
  * n_contrib (ws_rasterize) of the SAME frame, and the key_capacity the
  * workspace was sized with. opacity_logits may be NULL (sigma is read from
- * `opacity`). */
+ * the splat records). */
 ws_status ws_rasterize_backward(int64_t n, const float *means, const float *log_scales,
                                 const float *quats, const float *opacity_logits, const float *sh,
-                                const ws_camera *cam, const ws_config *cfg, const float *mean2d,
-                                const float *conic, const float *rgb, const float *opacity,
+                                const ws_camera *cam, const ws_config *cfg, const float *splats,
                                 const uint16_t *rect, const uint32_t *offsets,
                                 const uint32_t *tiles_touched, const uint32_t *vals,
                                 const uint32_t *ranges, const float *t_final, const uint32_t *n_contrib,
@@ -341,10 +348,9 @@ ws_status ws_rasterize_backward(int64_t n, const float *means, const float *log_
  * (and differentiated) together. Every view's image is bit-identical to the
  * single-view path; the batch reads the scene once instead of once per view.
  * Per-(view, Gaussian) arrays are view-major: entry (v, g) at v * n + g, with
- * the per-Gaussian layouts of the single-view calls (mean2d[V][n][4],
- * conic[V][n][3], depth[V][n], rgb[V][n][3], rect[V][n][4],
- * tiles_touched[V][n], offsets[V * n + 1]); opacity[n] is shared by all
- * views (0 for a Gaussian visible in none). Every entry is written, with
+ * the per-Gaussian layouts of the single-view calls (splats[V][n][12],
+ * depth[V][n], rect[V][n][4], tiles_touched[V][n], offsets[V * n + 1]).
+ * Every entry is written, with
  * zeros for a (view, Gaussian) that is culled, as in ws_preprocess. Tiles
  * are numbered in one global grid: view v's tiles follow those of views
  * 0..v-1, and the keys carry that global tile id (sort bits [0, 31 +
@@ -358,22 +364,19 @@ size_t ws_batch_workspace_bytes(int64_t n, int32_t views, const ws_camera *cams,
                                 const ws_config *cfg);
 ws_status ws_preprocess_batch(int64_t n, const float *means, const float *log_scales, const float *quats,
                               const float *opacity_logits, const float *sh, int32_t views,
-                              const ws_camera *cams, const ws_config *cfg, float *mean2d, float *conic,
-                              float *depth, float *rgb, float *opacity, uint16_t *rect,
-                              uint32_t *tiles_touched, void *stream);
+                              const ws_camera *cams, const ws_config *cfg, float *splats, float *depth,
+                              uint16_t *rect, uint32_t *tiles_touched, void *stream);
 ws_status ws_cull_batch(int64_t n, int32_t views, const ws_camera *cams, const ws_config *cfg,
                         const uint32_t *tiles_touched, const uint16_t *rect, const float *depth,
                         uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t key_capacity,
                         uint32_t *num_keys, void *workspace, void *stream);
 ws_status ws_rasterize_batch(const uint32_t *num_keys, const uint64_t *keys, const uint32_t *vals, int64_t n,
-                             const float *mean2d, const float *conic, const float *opacity, const float *rgb,
-                             int32_t views, const ws_camera *cams, const ws_config *cfg, uint32_t *ranges,
+                             const float *splats, int32_t views, const ws_camera *cams, const ws_config *cfg, uint32_t *ranges,
                              float *image, float *t_final, uint32_t *n_contrib, void *stream);
 /* Gradients summed over the views, in view order (deterministic). */
 ws_status ws_rasterize_backward_batch(int64_t n, const float *means, const float *log_scales,
                                       const float *quats, const float *sh, int32_t views,
-                                      const ws_camera *cams, const ws_config *cfg, const float *mean2d,
-                                      const float *conic, const float *rgb, const float *opacity,
+                                      const ws_camera *cams, const ws_config *cfg, const float *splats,
                                       const uint16_t *rect, const uint32_t *offsets,
                                       const uint32_t *tiles_touched, const uint32_t *vals,
                                       const uint32_t *ranges, const float *t_final,

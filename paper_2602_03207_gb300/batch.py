@@ -40,11 +40,8 @@ class BatchRenderer:
         d = torch.device(device)
         vn = max(self.V * self.n, 1)
         cap = max(self.key_capacity, 1)
-        self.mean2d = torch.empty((vn, 4), dtype=torch.float32, device=d)
-        self.conic = torch.empty((vn, 3), dtype=torch.float32, device=d)
+        self.splats = torch.empty((vn, capi.WS_SPLAT_FLOATS), dtype=torch.float32, device=d)
         self.depth = torch.empty(vn, dtype=torch.float32, device=d)
-        self.rgb = torch.empty((vn, 3), dtype=torch.float32, device=d)
-        self.opacity = torch.empty(max(self.n, 1), dtype=torch.float32, device=d)
         self.rect = torch.empty((vn, 4), dtype=torch.int16, device=d)
         self.tiles_touched = torch.empty(vn, dtype=torch.int32, device=d)
         self.offsets = torch.empty(self.V * self.n + 1, dtype=torch.int32, device=d)
@@ -78,11 +75,28 @@ class BatchRenderer:
     def sorted_vals(self):
         return self.vals_alt if self.sorted_in_alt else self.vals
 
+    # views of the view-major splat records (centre hi/lo, conic, sigma, colour)
+    @property
+    def mean2d(self):
+        return self.splats[:, 0:4]
+
+    @property
+    def conic(self):
+        return self.splats[:, 4:7]
+
+    @property
+    def opacity(self):
+        return self.splats[:, 7]
+
+    @property
+    def rgb(self):
+        return self.splats[:, 8:11]
+
     # ------------------------------------------------------------ stages
     def preprocess(self, scene, stream=None):
         capi.ws_preprocess_batch(self.n, scene["means"], scene["log_scales"], scene["quats"],
-                                 scene["opacity_logits"], scene["sh"], self.cams_arr, self.cfg, self.mean2d,
-                                 self.conic, self.depth, self.rgb, self.opacity, self.rect, self.tiles_touched, stream)
+                                 scene["opacity_logits"], scene["sh"], self.cams_arr, self.cfg, self.splats,
+                                 self.depth, self.rect, self.tiles_touched, stream)
 
     def cull(self, stream=None):
         capi.ws_cull_batch(self.n, self.cams_arr, self.cfg, self.tiles_touched, self.rect, self.depth, self.offsets,
@@ -93,9 +107,9 @@ class BatchRenderer:
                                           self.keys_alt, self.vals_alt, self.cfg, self.workspace, stream)
 
     def rasterize(self, stream=None):
-        capi.ws_rasterize_batch(self.num_keys, self.sorted_keys, self.sorted_vals, self.n, self.mean2d, self.conic,
-                                self.opacity, self.rgb, self.cams_arr, self.cfg, self.ranges, self.image,
-                                self.t_final, self.n_contrib, stream)
+        capi.ws_rasterize_batch(self.num_keys, self.sorted_keys, self.sorted_vals, self.n, self.splats,
+                                self.cams_arr, self.cfg, self.ranges, self.image, self.t_final, self.n_contrib,
+                                stream)
 
     def residual(self, target, stream=None):
         """d_image = image - target (gradient of 1/2 ||image - target||^2)."""
@@ -111,9 +125,9 @@ class BatchRenderer:
     def backward(self, scene, d_image, stream=None):
         g = self.grads
         capi.ws_rasterize_backward_batch(self.n, scene["means"], scene["log_scales"], scene["quats"], scene["sh"],
-                                         self.cams_arr, self.cfg, self.mean2d, self.conic, self.rgb, self.opacity,
-                                         self.rect, self.offsets, self.tiles_touched, self.sorted_vals, self.ranges,
-                                         self.t_final, self.n_contrib, d_image, self.key_capacity, g["means"],
+                                         self.cams_arr, self.cfg, self.splats, self.rect, self.offsets,
+                                         self.tiles_touched, self.sorted_vals, self.ranges, self.t_final,
+                                         self.n_contrib, d_image, self.key_capacity, g["means"],
                                          g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], self.workspace,
                                          stream)
         return {k: v[:self.n] for k, v in g.items()}

@@ -24,6 +24,8 @@ WS_OK, WS_ERR_INVALID_ARG, WS_ERR_CUDA, WS_ERR_CAPACITY, WS_ERR_TIMEOUT, WS_ERR_
 WS_FLAG_CAPACITY, WS_FLAG_TIMEOUT = 1, 2
 WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL, WS_CFG_SORT_LOOKBACK, WS_CFG_FIXED_RADIUS = 1, 2, 4, 8
 WS_CFG_SORT_SEGMENTED = 16
+WS_ABI_VERSION = 2
+WS_SPLAT_FLOATS = 12  # floats per splat record: centre hi/lo (4), conic (3), sigma, colour (3), 0
 
 EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_preprocess", "ws_cull",
            "ws_sort", "ws_sort_noalloc", "ws_sort_noalloc_max_keys", "ws_rasterize",
@@ -84,17 +86,17 @@ def lib():
             L.ws_status_string.restype = C.c_char_p
             L.ws_workspace_bytes.argtypes = [I64, I64, cam_p, cfg_p]
             L.ws_workspace_bytes.restype = C.c_size_t
-            L.ws_preprocess.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P, P]
+            L.ws_preprocess.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
             L.ws_cull.argtypes = [I64, P, P, P, cam_p, cfg_p, P, P, P, I64, P, P, P]
             L.ws_sort.argtypes = [P, I64, I32, I32, P, P, P, P, cfg_p, P, C.POINTER(I32), P]
-            L.ws_rasterize.argtypes = [P, P, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
+            L.ws_rasterize.argtypes = [P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
             L.ws_preprocess_packed.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P]
             L.ws_quads_workspace_bytes.argtypes = [I64, I64, cam_p, cfg_p]
             L.ws_quads_workspace_bytes.restype = C.c_size_t
-            L.ws_render_quads.argtypes = [I64, P, P, P, P, P, P, cam_p, cfg_p, I64, P, P, P, P, P, P, P, P, P]
+            L.ws_render_quads.argtypes = [I64, P, P, P, cam_p, cfg_p, I64, P, P, P, P, P, P, P, P, P]
             L.ws_rasterize_packed.argtypes = [P, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P]
-            L.ws_rasterize_backward.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P, P, P,
-                                                P, P, P, I64, P, P, P, P, P, P, P]
+            L.ws_rasterize_backward.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P, P,
+                                                P, I64, P, P, P, P, P, P, P]
             L.ws_sort_test_stalled_tile.argtypes = [P, I64, I32, I32, P, P, P, P, cfg_p, P, I32, C.POINTER(I32), P]
             L.ws_sort_test_stalled_tile.restype = I32
             L.ws_sort_noalloc.argtypes = [P, I64, I32, I32, P, P, P, P, I32, C.POINTER(I32), P]
@@ -104,10 +106,10 @@ def lib():
             L.ws_batch_max_views.restype = I32
             L.ws_batch_workspace_bytes.argtypes = [I64, I32, cam_p, I64, cfg_p]
             L.ws_batch_workspace_bytes.restype = C.c_size_t
-            L.ws_preprocess_batch.argtypes = [I64, P, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P, P, P, P]
+            L.ws_preprocess_batch.argtypes = [I64, P, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P]
             L.ws_cull_batch.argtypes = [I64, I32, cam_p, cfg_p, P, P, P, P, P, P, I64, P, P, P]
-            L.ws_rasterize_batch.argtypes = [P, P, P, I64, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P]
-            L.ws_rasterize_backward_batch.argtypes = [I64, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P, P, P, P,
+            L.ws_rasterize_batch.argtypes = [P, P, P, I64, P, I32, cam_p, cfg_p, P, P, P, P, P]
+            L.ws_rasterize_backward_batch.argtypes = [I64, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P,
                                                       P, P, P, P, I64, P, P, P, P, P, P, P]
             L.ws_image_residual.argtypes = [I64, P, P, P, P]
             for name in ("ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
@@ -144,12 +146,11 @@ def ws_workspace_bytes(n, key_capacity, cam: Camera, cfg: Config) -> int:
     return int(lib().ws_workspace_bytes(int(n), int(key_capacity), C.byref(cam), C.byref(cfg)))
 
 
-def ws_preprocess(n, means, log_scales, quats, opacity_logits, sh, cam, cfg, mean2d, conic, depth,
-                  rgb, opacity, rect, tiles_touched, stream=None):
+def ws_preprocess(n, means, log_scales, quats, opacity_logits, sh, cam, cfg, splats, depth, rect, tiles_touched,
+                  stream=None):
     _check("ws_preprocess", lib().ws_preprocess(
         int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh),
-        C.byref(cam), C.byref(cfg), _ptr(mean2d), _ptr(conic), _ptr(depth), _ptr(rgb),
-        _ptr(opacity), _ptr(rect), _ptr(tiles_touched), _stream(stream)))
+        C.byref(cam), C.byref(cfg), _ptr(splats), _ptr(depth), _ptr(rect), _ptr(tiles_touched), _stream(stream)))
 
 
 def ws_cull(n, tiles_touched, rect, depth, cam, cfg, offsets, keys, vals, key_capacity, num_keys,
@@ -194,11 +195,9 @@ def ws_sort_noalloc(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys
     return bool(in_alt.value)
 
 
-def ws_rasterize(num_keys, keys, vals, mean2d, conic, opacity, rgb, cam, cfg, ranges, image,
-                 t_final, n_contrib, stream=None):
+def ws_rasterize(num_keys, keys, vals, splats, cam, cfg, ranges, image, t_final, n_contrib, stream=None):
     _check("ws_rasterize", lib().ws_rasterize(
-        _ptr(num_keys), _ptr(keys), _ptr(vals), _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb),
-        C.byref(cam), C.byref(cfg), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib),
+        _ptr(num_keys), _ptr(keys), _ptr(vals), _ptr(splats), C.byref(cam), C.byref(cfg), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib),
         _stream(stream)))
 
 
@@ -221,21 +220,20 @@ def ws_quads_workspace_bytes(n, key_capacity, cam, cfg):
     return int(lib().ws_quads_workspace_bytes(int(n), int(key_capacity), C.byref(cam), C.byref(cfg)))
 
 
-def ws_render_quads(n, mean2d, conic, opacity, rgb, depth, tiles_touched, cam, cfg, key_capacity, keys, vals,
-                    keys_alt, vals_alt, num_keys, image, t_final, workspace, stream=None):
+def ws_render_quads(n, splats, depth, tiles_touched, cam, cfg, key_capacity, keys, vals, keys_alt, vals_alt,
+                    num_keys, image, t_final, workspace, stream=None):
     _check("ws_render_quads", lib().ws_render_quads(
-        int(n), _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb), _ptr(depth), _ptr(tiles_touched),
+        int(n), _ptr(splats), _ptr(depth), _ptr(tiles_touched),
         C.byref(cam), C.byref(cfg), int(key_capacity), _ptr(keys), _ptr(vals), _ptr(keys_alt), _ptr(vals_alt),
         _ptr(num_keys), _ptr(image), _ptr(t_final), _ptr(workspace), _stream(stream)))
 
 
-def ws_rasterize_backward(n, means, log_scales, quats, opacity_logits, sh, cam, cfg, mean2d, conic, rgb,
-                          opacity, rect, offsets, tiles_touched, vals, ranges, t_final, n_contrib, d_image,
-                          key_capacity, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, workspace,
-                          stream=None):
+def ws_rasterize_backward(n, means, log_scales, quats, opacity_logits, sh, cam, cfg, splats, rect, offsets,
+                          tiles_touched, vals, ranges, t_final, n_contrib, d_image, key_capacity, d_means,
+                          d_log_scales, d_quats, d_opacity_logits, d_sh, workspace, stream=None):
     _check("ws_rasterize_backward", lib().ws_rasterize_backward(
         int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh), C.byref(cam),
-        C.byref(cfg), _ptr(mean2d), _ptr(conic), _ptr(rgb), _ptr(opacity), _ptr(rect), _ptr(offsets),
+        C.byref(cfg), _ptr(splats), _ptr(rect), _ptr(offsets),
         _ptr(tiles_touched), _ptr(vals), _ptr(ranges), _ptr(t_final), _ptr(n_contrib), _ptr(d_image),
         int(key_capacity), _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats), _ptr(d_opacity_logits),
         _ptr(d_sh), _ptr(workspace), _stream(stream)))
@@ -266,12 +264,11 @@ def ws_batch_workspace_bytes(n, cams_arr, key_capacity, cfg) -> int:
     return int(lib().ws_batch_workspace_bytes(int(n), len(cams_arr), cams_arr, int(key_capacity), C.byref(cfg)))
 
 
-def ws_preprocess_batch(n, means, log_scales, quats, opacity_logits, sh, cams_arr, cfg, mean2d, conic, depth, rgb,
-                        opacity, rect, tiles_touched, stream=None):
+def ws_preprocess_batch(n, means, log_scales, quats, opacity_logits, sh, cams_arr, cfg, splats, depth, rect,
+                        tiles_touched, stream=None):
     _check("ws_preprocess_batch", lib().ws_preprocess_batch(
         int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh), len(cams_arr),
-        cams_arr, C.byref(cfg), _ptr(mean2d), _ptr(conic), _ptr(depth), _ptr(rgb), _ptr(opacity), _ptr(rect),
-        _ptr(tiles_touched), _stream(stream)))
+        cams_arr, C.byref(cfg), _ptr(splats), _ptr(depth), _ptr(rect), _ptr(tiles_touched), _stream(stream)))
 
 
 def ws_cull_batch(n, cams_arr, cfg, tiles_touched, rect, depth, offsets, keys, vals, key_capacity, num_keys,
@@ -281,20 +278,19 @@ def ws_cull_batch(n, cams_arr, cfg, tiles_touched, rect, depth, offsets, keys, v
         _ptr(keys), _ptr(vals), int(key_capacity), _ptr(num_keys), _ptr(workspace), _stream(stream)))
 
 
-def ws_rasterize_batch(num_keys, keys, vals, n, mean2d, conic, opacity, rgb, cams_arr, cfg, ranges, image, t_final,
-                       n_contrib, stream=None):
+def ws_rasterize_batch(num_keys, keys, vals, n, splats, cams_arr, cfg, ranges, image, t_final, n_contrib,
+                       stream=None):
     _check("ws_rasterize_batch", lib().ws_rasterize_batch(
-        _ptr(num_keys), _ptr(keys), _ptr(vals), int(n), _ptr(mean2d), _ptr(conic), _ptr(opacity), _ptr(rgb),
-        len(cams_arr), cams_arr, C.byref(cfg), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib),
+        _ptr(num_keys), _ptr(keys), _ptr(vals), int(n), _ptr(splats), len(cams_arr), cams_arr, C.byref(cfg), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib),
         _stream(stream)))
 
 
-def ws_rasterize_backward_batch(n, means, log_scales, quats, sh, cams_arr, cfg, mean2d, conic, rgb, opacity, rect,
-                                offsets, tiles_touched, vals, ranges, t_final, n_contrib, d_image, key_capacity,
-                                d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, workspace, stream=None):
+def ws_rasterize_backward_batch(n, means, log_scales, quats, sh, cams_arr, cfg, splats, rect, offsets,
+                                tiles_touched, vals, ranges, t_final, n_contrib, d_image, key_capacity, d_means,
+                                d_log_scales, d_quats, d_opacity_logits, d_sh, workspace, stream=None):
     _check("ws_rasterize_backward_batch", lib().ws_rasterize_backward_batch(
         int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(sh), len(cams_arr), cams_arr, C.byref(cfg),
-        _ptr(mean2d), _ptr(conic), _ptr(rgb), _ptr(opacity), _ptr(rect), _ptr(offsets), _ptr(tiles_touched),
+        _ptr(splats), _ptr(rect), _ptr(offsets), _ptr(tiles_touched),
         _ptr(vals), _ptr(ranges), _ptr(t_final), _ptr(n_contrib), _ptr(d_image), int(key_capacity), _ptr(d_means),
         _ptr(d_log_scales), _ptr(d_quats), _ptr(d_opacity_logits), _ptr(d_sh), _ptr(workspace), _stream(stream)))
 

@@ -136,18 +136,17 @@ size_t ws_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera* cam,
 
 ws_status ws_preprocess(int64_t n, const float* means, const float* log_scales, const float* quats,
                         const float* opacity_logits, const float* sh, const ws_camera* cam,
-                        const ws_config* cfg, float* mean2d, float* conic, float* depth, float* rgb,
-                        float* opacity, uint16_t* rect, uint32_t* tiles_touched, void* stream) {
+                        const ws_config* cfg, float* splats, float* depth, uint16_t* rect,
+                        uint32_t* tiles_touched, void* stream) {
     if (n < 0 || n >= (int64_t(1) << 32) || !valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
     if (n == 0) return WS_OK;
-    const void* ptrs[] = {means, log_scales, quats, opacity_logits, sh, mean2d, conic, depth,
-                          rgb, opacity, rect, tiles_touched};
+    const void* ptrs[] = {means, log_scales, quats, opacity_logits, sh, splats, depth, rect, tiles_touched};
     for (const void* p : ptrs)
         if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
     const Frame f = make_frame(cam, cfg);
     if (f.TX > 65535 || f.TY > 65535) return WS_ERR_UNSUPPORTED;
     return cuda_status(ws::launch_preprocess(n, means, log_scales, quats, opacity_logits, sh, f,
-                                             mean2d, conic, depth, rgb, opacity, rect, tiles_touched,
+                                             splats, depth, rect, tiles_touched,
                                              static_cast<cudaStream_t>(stream)));
 }
 
@@ -260,15 +259,14 @@ ws_status ws_sort_noalloc(const uint32_t* num_keys, int64_t key_capacity, int32_
 }
 
 ws_status ws_rasterize(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals,
-                       const float* mean2d, const float* conic, const float* opacity, const float* rgb,
-                       const ws_camera* cam, const ws_config* cfg, uint32_t* ranges, float* image,
-                       float* t_final, uint32_t* n_contrib, void* stream) {
+                       const float* splats, const ws_camera* cam, const ws_config* cfg, uint32_t* ranges,
+                       float* image, float* t_final, uint32_t* n_contrib, void* stream) {
     if (!valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
-    const void* ptrs[] = {num_keys, keys, vals, mean2d, conic, opacity, rgb, ranges, image, t_final, n_contrib};
+    const void* ptrs[] = {num_keys, keys, vals, splats, ranges, image, t_final, n_contrib};
     for (const void* p : ptrs)
         if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
     const Frame f = make_frame(cam, cfg);
-    return cuda_status(ws::launch_rasterize(num_keys, 0, keys, vals, mean2d, conic, opacity, rgb, f, ranges,
+    return cuda_status(ws::launch_rasterize(num_keys, 0, keys, vals, splats, f, ranges,
                                             image, t_final, n_contrib, static_cast<cudaStream_t>(stream)));
 }
 
@@ -309,8 +307,8 @@ size_t ws_quads_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera
     return ws::quad_layout(n, key_capacity, (int64_t)f.TX * f.TY).total;
 }
 
-ws_status ws_render_quads(int64_t n, const float* mean2d, const float* conic, const float* opacity,
-                          const float* rgb, const float* depth, const uint32_t* tiles_touched, const ws_camera* cam,
+ws_status ws_render_quads(int64_t n, const float* splats, const float* depth, const uint32_t* tiles_touched,
+                          const ws_camera* cam,
                           const ws_config* cfg, int64_t key_capacity, uint64_t* keys, uint32_t* vals,
                           uint64_t* keys_alt, uint32_t* vals_alt, uint32_t* num_keys, float* image, float* t_final,
                           void* workspace, void* stream) {
@@ -321,7 +319,7 @@ ws_status ws_render_quads(int64_t n, const float* mean2d, const float* conic, co
     for (const void* p : ptrs)
         if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
     if (n > 0) {
-        const void* in[] = {mean2d, conic, opacity, rgb, depth, tiles_touched};
+        const void* in[] = {splats, depth, tiles_touched};
         for (const void* p : in)
             if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
     }
@@ -332,22 +330,21 @@ ws_status ws_render_quads(int64_t n, const float* mean2d, const float* conic, co
     }
     const Frame f = make_frame(cam, cfg);
     if (f.TX > 65535 || f.TY > 65535) return WS_ERR_UNSUPPORTED;
-    return cuda_status(ws::launch_render_quads(n, mean2d, conic, opacity, rgb, depth, tiles_touched, f, key_capacity,
+    return cuda_status(ws::launch_render_quads(n, splats, depth, tiles_touched, f, key_capacity,
                                                keys, vals, keys_alt, vals_alt, num_keys, image, t_final, workspace,
                                                static_cast<cudaStream_t>(stream)));
 }
 
 ws_status ws_rasterize_backward(int64_t n, const float* means, const float* log_scales,
                                 const float* quats, const float* opacity_logits, const float* sh,
-                                const ws_camera* cam, const ws_config* cfg, const float* mean2d,
-                                const float* conic, const float* rgb, const float* opacity,
+                                const ws_camera* cam, const ws_config* cfg, const float* splats,
                                 const uint16_t* rect, const uint32_t* offsets,
                                 const uint32_t* tiles_touched, const uint32_t* vals,
                                 const uint32_t* ranges, const float* t_final, const uint32_t* n_contrib,
                                 const float* d_image, int64_t key_capacity, float* d_means,
                                 float* d_log_scales, float* d_quats, float* d_opacity_logits,
                                 float* d_sh, void* workspace, void* stream) {
-    (void)opacity_logits;  // sigma is read back from `opacity`
+    (void)opacity_logits;  // sigma is read back from the splat records
     if (n < 0 || n >= (int64_t(1) << 32) || key_capacity < 0 || key_capacity >= (int64_t(1) << 31))
         return WS_ERR_INVALID_ARG;
     if (!valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
@@ -355,7 +352,7 @@ ws_status ws_rasterize_backward(int64_t n, const float* means, const float* log_
     for (const void* p : ptrs)
         if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
     if (n > 0) {
-        const void* per[] = {means, log_scales, quats, sh, mean2d, conic, rgb, opacity, rect,
+        const void* per[] = {means, log_scales, quats, sh, splats, rect,
                              tiles_touched, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
         for (const void* p : per)
             if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
@@ -363,7 +360,7 @@ ws_status ws_rasterize_backward(int64_t n, const float* means, const float* log_
     if (key_capacity > 0 && (!vals || !aligned16(vals))) return WS_ERR_INVALID_ARG;
     const Frame f = make_frame(cam, cfg);
     char* ws_base = static_cast<char*>(workspace);
-    return cuda_status(ws::launch_backward(n, means, log_scales, quats, sh, f, mean2d, conic, rgb, opacity,
+    return cuda_status(ws::launch_backward(n, means, log_scales, quats, sh, f, splats,
                                            rect, offsets, tiles_touched, vals, ranges, t_final, n_contrib,
                                            d_image, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
                                            key_capacity, ws_base + layout(0, key_capacity).bwd,
@@ -383,17 +380,16 @@ int32_t ws_batch_max_views(void) { return ws::kMaxViews; }
 
 ws_status ws_preprocess_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
                               const float* opacity_logits, const float* sh, int32_t views, const ws_camera* cams,
-                              const ws_config* cfg, float* mean2d, float* conic, float* depth, float* rgb,
-                              float* opacity, uint16_t* rect, uint32_t* tiles_touched, void* stream) {
+                              const ws_config* cfg, float* splats, float* depth, uint16_t* rect,
+                              uint32_t* tiles_touched, void* stream) {
     ws::FrameTable ft;
     if (n < 0 || !make_table(views, cams, cfg, ft) || n * views >= (int64_t(1) << 32)) return WS_ERR_INVALID_ARG;
     if (n == 0) return WS_OK;
-    const void* ptrs[] = {means, log_scales, quats, opacity_logits, sh, mean2d, conic, depth,
-                          rgb, opacity, rect, tiles_touched};
+    const void* ptrs[] = {means, log_scales, quats, opacity_logits, sh, splats, depth, rect, tiles_touched};
     for (const void* p : ptrs)
         if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
-    return cuda_status(ws::launch_preprocess_batch(n, means, log_scales, quats, opacity_logits, sh, ft, mean2d,
-                                                   conic, depth, rgb, opacity, rect, tiles_touched,
+    return cuda_status(ws::launch_preprocess_batch(n, means, log_scales, quats, opacity_logits, sh, ft, splats,
+                                                   depth, rect, tiles_touched,
                                                    static_cast<cudaStream_t>(stream)));
 }
 
@@ -422,22 +418,20 @@ ws_status ws_cull_batch(int64_t n, int32_t views, const ws_camera* cams, const w
 }
 
 ws_status ws_rasterize_batch(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals, int64_t n,
-                             const float* mean2d, const float* conic, const float* opacity, const float* rgb,
-                             int32_t views, const ws_camera* cams, const ws_config* cfg, uint32_t* ranges,
+                             const float* splats, int32_t views, const ws_camera* cams, const ws_config* cfg, uint32_t* ranges,
                              float* image, float* t_final, uint32_t* n_contrib, void* stream) {
     ws::FrameTable ft;
     if (n < 0 || !make_table(views, cams, cfg, ft)) return WS_ERR_INVALID_ARG;
-    const void* ptrs[] = {num_keys, keys, vals, mean2d, conic, opacity, rgb, ranges, image, t_final, n_contrib};
+    const void* ptrs[] = {num_keys, keys, vals, splats, ranges, image, t_final, n_contrib};
     for (const void* p : ptrs)
         if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
-    return cuda_status(ws::launch_rasterize_batch(num_keys, keys, vals, n, mean2d, conic, opacity, rgb, ft, ranges,
+    return cuda_status(ws::launch_rasterize_batch(num_keys, keys, vals, n, splats, ft, ranges,
                                                   image, t_final, n_contrib, static_cast<cudaStream_t>(stream)));
 }
 
 ws_status ws_rasterize_backward_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
                                       const float* sh, int32_t views, const ws_camera* cams, const ws_config* cfg,
-                                      const float* mean2d, const float* conic, const float* rgb,
-                                      const float* opacity, const uint16_t* rect, const uint32_t* offsets,
+                                      const float* splats, const uint16_t* rect, const uint32_t* offsets,
                                       const uint32_t* tiles_touched, const uint32_t* vals, const uint32_t* ranges,
                                       const float* t_final, const uint32_t* n_contrib, const float* d_image,
                                       int64_t key_capacity, float* d_means, float* d_log_scales, float* d_quats,
@@ -449,14 +443,14 @@ ws_status ws_rasterize_backward_batch(int64_t n, const float* means, const float
     for (const void* p : ptrs)
         if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
     if (n > 0) {
-        const void* per[] = {means, log_scales, quats, sh, mean2d, conic, rgb, opacity, rect,
+        const void* per[] = {means, log_scales, quats, sh, splats, rect,
                              tiles_touched, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
         for (const void* p : per)
             if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
     }
     if (key_capacity > 0 && (!vals || !aligned16(vals))) return WS_ERR_INVALID_ARG;
     char* ws_base = static_cast<char*>(workspace);
-    return cuda_status(ws::launch_backward_batch(n, means, log_scales, quats, sh, ft, mean2d, conic, rgb, opacity,
+    return cuda_status(ws::launch_backward_batch(n, means, log_scales, quats, sh, ft, splats,
                                                  rect, offsets, tiles_touched, vals, ranges, t_final, n_contrib,
                                                  d_image, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
                                                  key_capacity, ws_base + layout(0, key_capacity).bwd,

@@ -36,14 +36,12 @@ namespace {
 
 template <int TS>
 __global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS)
-k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-            const float4* __restrict__ mean2d, const float* __restrict__ conic,
-            const float* __restrict__ opacity, const float* __restrict__ rgb,
+k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, const float4* __restrict__ splats,
             const uint2* __restrict__ rect, const uint32_t* __restrict__ offsets, const Frame f,
             const float* __restrict__ t_final, const uint32_t* __restrict__ n_contrib,
             const float* __restrict__ d_image, float* __restrict__ partials) {
     pdl_wait();
-    blend_bwd_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, mean2d, conic, opacity, rgb, rect,
+    blend_bwd_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, splats, rect,
                        [offsets](uint32_t g) { return __ldg(offsets + g); }, t_final, n_contrib, d_image, partials);
 }
 
@@ -52,8 +50,7 @@ constexpr int kPbThreads = 128;
 __global__ void __launch_bounds__(kPbThreads, 8)
 k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __restrict__ log_scales,
                  const float4* __restrict__ quats, const float4* __restrict__ sh, const Frame f,
-                 const float* __restrict__ rgb, const float* __restrict__ opacity,
-                 const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ touched,
+                 const float4* __restrict__ splats, const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ touched,
                  uint32_t cap, const float* __restrict__ partials, float* __restrict__ d_means,
                  float* __restrict__ d_log_scales, float4* __restrict__ d_quats,
                  float* __restrict__ d_logits, float4* __restrict__ d_sh) {
@@ -96,12 +93,13 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
         X[0] = __ldg(means + 3 * i);
         X[1] = __ldg(means + 3 * i + 1);
         X[2] = __ldg(means + 3 * i + 2);
-        const float sig = __ldg(opacity + i);
+        const float sig = __ldg(splats + kSplatVec4 * i + 1).w;
         const float4 q4 = __ldg(quats + i);
         const float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1), __ldg(log_scales + 3 * i + 2)};
-        col[0] = __ldg(rgb + 3 * i);
-        col[1] = __ldg(rgb + 3 * i + 1);
-        col[2] = __ldg(rgb + 3 * i + 2);
+        const float4 cl = __ldg(splats + kSplatVec4 * i + 2);
+        col[0] = cl.x;
+        col[1] = cl.y;
+        col[2] = cl.z;
         // slot-ordered sum of this Gaussian's pair records
         const float* src = partials + (size_t)first * kPart;
         for (uint32_t s = 0; s < nrec; ++s)
@@ -167,8 +165,7 @@ size_t backward_scratch_bytes(int64_t key_capacity) {
 }
 
 cudaError_t launch_backward(int64_t n, const float* means, const float* log_scales, const float* quats,
-                            const float* sh, const Frame& f, const float* mean2d, const float* conic,
-                            const float* rgb, const float* opacity, const uint16_t* rect,
+                            const float* sh, const Frame& f, const float* splats, const uint16_t* rect,
                             const uint32_t* offsets, const uint32_t* tiles_touched,
                             const uint32_t* vals, const uint32_t* ranges, const float* t_final,
                             const uint32_t* n_contrib, const float* d_image, float* d_means,
@@ -177,22 +174,22 @@ cudaError_t launch_backward(int64_t n, const float* means, const float* log_scal
     float* partials = static_cast<float*>(scratch);
     const int ntiles = f.TX * f.TY;
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
-    const float4* m4 = reinterpret_cast<const float4*>(mean2d);
+    const float4* s4 = reinterpret_cast<const float4*>(splats);
     const uint2* rc = reinterpret_cast<const uint2*>(rect);
     cudaError_t e = cudaSuccess;
     if (ntiles > 0) {
         switch (f.TS) {
             case 8:
-                e = launch_pdl(k_blend_bwd<8>, dim3(ntiles), dim3(64), 0, stream, r2, vals, m4, conic, opacity, rgb,
-                               rc, offsets, f, t_final, n_contrib, d_image, partials);
+                e = launch_pdl(k_blend_bwd<8>, dim3(ntiles), dim3(64), 0, stream, r2, vals, s4, rc, offsets, f,
+                               t_final, n_contrib, d_image, partials);
                 break;
             case 16:
-                e = launch_pdl(k_blend_bwd<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, m4, conic, opacity,
-                               rgb, rc, offsets, f, t_final, n_contrib, d_image, partials);
+                e = launch_pdl(k_blend_bwd<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, s4, rc, offsets, f,
+                               t_final, n_contrib, d_image, partials);
                 break;
             case 32:
-                e = launch_pdl(k_blend_bwd<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, m4, conic, opacity,
-                               rgb, rc, offsets, f, t_final, n_contrib, d_image, partials);
+                e = launch_pdl(k_blend_bwd<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, s4, rc, offsets, f,
+                               t_final, n_contrib, d_image, partials);
                 break;
             default:
                 return cudaErrorInvalidValue;
@@ -202,7 +199,7 @@ cudaError_t launch_backward(int64_t n, const float* means, const float* log_scal
     if (n > 0) {
         const int64_t blocks = (n + kPbThreads - 1) / kPbThreads;
         e = launch_pdl(k_preprocess_bwd, dim3((unsigned)blocks), dim3(kPbThreads), 0, stream, n, means, log_scales,
-                       reinterpret_cast<const float4*>(quats), reinterpret_cast<const float4*>(sh), f, rgb, opacity,
+                       reinterpret_cast<const float4*>(quats), reinterpret_cast<const float4*>(sh), f, s4,
                        offsets, tiles_touched, (uint32_t)key_capacity, (const float*)partials, d_means, d_log_scales,
                        reinterpret_cast<float4*>(d_quats), d_logits, reinterpret_cast<float4*>(d_sh));
     }

@@ -29,9 +29,8 @@ constexpr int kBatchThreads = 128;
 __global__ void __launch_bounds__(kBatchThreads)
 k_preprocess_batch(int64_t n, const float* __restrict__ means, const float* __restrict__ log_scales,
                    const float4* __restrict__ quats, const float* __restrict__ logits,
-                   const float4* __restrict__ sh, const FrameTable ft, float4* __restrict__ mean2d,
-                   float* __restrict__ conic, float* __restrict__ depth, float* __restrict__ rgb,
-                   float* __restrict__ opacity, uint2* __restrict__ rect, uint32_t* __restrict__ tiles_touched) {
+                   const float4* __restrict__ sh, const FrameTable ft, float4* __restrict__ splats,
+                   float* __restrict__ depth, uint2* __restrict__ rect, uint32_t* __restrict__ tiles_touched) {
     __shared__ __align__(16) float s_sh[kBatchThreads / kWarp][kWarp * kShPad];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * kBatchThreads + threadIdx.x;
@@ -66,8 +65,6 @@ k_preprocess_batch(int64_t n, const float* __restrict__ means, const float* __re
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
     }
-    float sigma = 0.f;
-    bool any_view = false;
     for (int v = 0; v < ft.views; ++v) {
         const Frame& f = ft.f[v];
         const int64_t o = (int64_t)v * n + i;
@@ -84,36 +81,26 @@ k_preprocess_batch(int64_t n, const float* __restrict__ means, const float* __re
             const float dx = x - f.campos[0], dy = y - f.campos[1], dz = z - f.campos[2];
             const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
             sh_eval(dx * inv, dy * inv, dz * inv, stage + lane * kShPad, c3);
-            sigma = P.sigma;
-            any_view = true;
         }
         // every lane stores its entries (zeros where culled): whole sectors
         if (valid) {
-            mean2d[o] = vis ? P.m4 : make_float4(0.f, 0.f, 0.f, 0.f);
-            conic[3 * o] = vis ? P.ca : 0.f;
-            conic[3 * o + 1] = vis ? P.cb : 0.f;
-            conic[3 * o + 2] = vis ? P.cc : 0.f;
-            rgb[3 * o] = c3.x;
-            rgb[3 * o + 1] = c3.y;
-            rgb[3 * o + 2] = c3.z;
+            store_splat(splats + kSplatVec4 * o, vis, P, c3);
             rect[o] = vis ? make_uint2(P.x0 | (P.y0 << 16), P.x1 | (P.y1 << 16)) : make_uint2(0u, 0u);
             tiles_touched[o] = vis ? (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1) : 0u;
         }
     }
-    if (valid) opacity[i] = any_view ? sigma : 0.f;
 }
 
 template <int TS>
 __global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS)
 k_blend_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, int64_t n,
-              const float4* __restrict__ mean2d, const float* __restrict__ conic,
-              const float* __restrict__ opacity, const float* __restrict__ rgb, const FrameTable ft,
+              const float4* __restrict__ splats, const FrameTable ft,
               float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
     pdl_wait();
     const uint32_t t = blockIdx.x;
     const int v = view_of_tile(ft.tile_off, ft.views, t);
     const uint64_t vo = (uint64_t)v * (uint64_t)n, po = ft.pix_off[v];
-    const FloatSplats sp{mean2d + vo, conic + 3 * vo, opacity, rgb + 3 * vo};
+    const FloatSplats sp{splats + kSplatVec4 * vo};
     blend_tile<TS>(ft.f[v], (int)(t - ft.tile_off[v]), ranges[t], vals, sp, image + 3 * po, t_final + po,
                    n_contrib + po);
 }
@@ -121,8 +108,7 @@ k_blend_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ val
 template <int TS>
 __global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS)
 k_blend_bwd_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, int64_t n,
-                  const float4* __restrict__ mean2d, const float* __restrict__ conic,
-                  const float* __restrict__ opacity, const float* __restrict__ rgb, const uint2* __restrict__ rect,
+                  const float4* __restrict__ splats, const uint2* __restrict__ rect,
                   const uint32_t* __restrict__ offsets, const FrameTable ft, const float* __restrict__ t_final,
                   const uint32_t* __restrict__ n_contrib, const float* __restrict__ d_image,
                   float* __restrict__ partials) {
@@ -131,16 +117,15 @@ k_blend_bwd_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__
     const int v = view_of_tile(ft.tile_off, ft.views, t);
     const uint64_t vo = (uint64_t)v * (uint64_t)n, po = ft.pix_off[v];
     const uint32_t* voff = offsets + vo;
-    blend_bwd_tile<TS>(ft.f[v], (int)(t - ft.tile_off[v]), ranges[t], vals, mean2d + vo, conic + 3 * vo, opacity,
-                       rgb + 3 * vo, rect + vo, [voff](uint32_t g) { return __ldg(voff + g); }, t_final + po,
+    blend_bwd_tile<TS>(ft.f[v], (int)(t - ft.tile_off[v]), ranges[t], vals, splats + kSplatVec4 * vo, rect + vo, [voff](uint32_t g) { return __ldg(voff + g); }, t_final + po,
                        n_contrib + po, d_image + 3 * po, partials);
 }
 
 __global__ void __launch_bounds__(kBatchThreads)
 k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* __restrict__ log_scales,
                        const float4* __restrict__ quats, const float4* __restrict__ sh, const FrameTable ft,
-                       const float* __restrict__ rgb, const float* __restrict__ opacity,
-                       const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ touched,
+                       const float4* __restrict__ splats, const uint32_t* __restrict__ offsets,
+                       const uint32_t* __restrict__ touched,
                        uint32_t cap, const float* __restrict__ partials, float* __restrict__ d_means,
                        float* __restrict__ d_log_scales, float4* __restrict__ d_quats,
                        float* __restrict__ d_logits, float4* __restrict__ d_sh) {
@@ -156,7 +141,6 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
 
     float X[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f};
     float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float sig = 0.f;
     if (valid) {
         X[0] = __ldg(means + 3 * i);
         X[1] = __ldg(means + 3 * i + 1);
@@ -165,7 +149,6 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
         ls[1] = __ldg(log_scales + 3 * i + 1);
         ls[2] = __ldg(log_scales + 3 * i + 2);
         q4 = __ldg(quats + i);
-        sig = __ldg(opacity + i);
     }
     // stage this warp's SH coefficients; zero the SH gradient accumulators
     float* stage = s_sh[warp];
@@ -207,10 +190,12 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
         for (uint32_t s = 0; s < nrec; ++s)
 #pragma unroll
             for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
+        const float sig = __ldg(splats + kSplatVec4 * o + 1).w;  // sigma (the same in every view)
         glogit += pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
         const Frame& f = ft.f[v];
         splat_adjoint(f, X, q4, ls, pr, gm, gls, gq);
-        const float col[3] = {__ldg(rgb + 3 * o), __ldg(rgb + 3 * o + 1), __ldg(rgb + 3 * o + 2)};
+        const float4 cl = __ldg(splats + kSplatVec4 * o + 2);
+        const float col[3] = {cl.x, cl.y, cl.z};
         sh_adjoint(f, X, stage + lane * kShPad, col, pr, gm, gsh, true);
     }
     __syncwarp();
@@ -253,45 +238,41 @@ __global__ void k_residual(int64_t count, const float4* __restrict__ image, cons
 }  // namespace
 
 cudaError_t launch_preprocess_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
-                                    const float* logits, const float* sh, const FrameTable& ft, float* mean2d,
-                                    float* conic, float* depth, float* rgb, float* opacity, uint16_t* rect,
-                                    uint32_t* tiles_touched, cudaStream_t stream) {
+                                    const float* logits, const float* sh, const FrameTable& ft, float* splats,
+                                    float* depth, uint16_t* rect, uint32_t* tiles_touched, cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
     const int64_t blocks = (n + kBatchThreads - 1) / kBatchThreads;
     return launch_pdl(k_preprocess_batch, dim3((unsigned)blocks), dim3(kBatchThreads), 0, stream, n, means,
                       log_scales, reinterpret_cast<const float4*>(quats), logits, reinterpret_cast<const float4*>(sh),
-                      ft, reinterpret_cast<float4*>(mean2d), conic, depth, rgb, opacity,
-                      reinterpret_cast<uint2*>(rect), tiles_touched);
+                      ft, reinterpret_cast<float4*>(splats), depth, reinterpret_cast<uint2*>(rect), tiles_touched);
 }
 
 cudaError_t launch_rasterize_batch(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals, int64_t n,
-                                   const float* mean2d, const float* conic, const float* opacity, const float* rgb,
-                                   const FrameTable& ft, uint32_t* ranges, float* image, float* t_final,
+                                   const float* splats, const FrameTable& ft, uint32_t* ranges, float* image, float* t_final,
                                    uint32_t* n_contrib, cudaStream_t stream) {
     const uint32_t ntiles = ft.tile_off[ft.views];
     if (ntiles == 0) return cudaSuccess;
     cudaError_t e = launch_tile_ranges(keys, num_keys, ranges, ntiles, stream);
     if (e != cudaSuccess) return e;
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
-    const float4* m4 = reinterpret_cast<const float4*>(mean2d);
+    const float4* s4 = reinterpret_cast<const float4*>(splats);
     switch (ft.f[0].TS) {
         case 8:
-            return launch_pdl(k_blend_batch<8>, dim3(ntiles), dim3(64), 0, stream, r2, vals, n, m4, conic, opacity,
-                              rgb, ft, image, t_final, n_contrib);
+            return launch_pdl(k_blend_batch<8>, dim3(ntiles), dim3(64), 0, stream, r2, vals, n, s4, ft, image,
+                              t_final, n_contrib);
         case 16:
-            return launch_pdl(k_blend_batch<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, m4, conic, opacity,
-                              rgb, ft, image, t_final, n_contrib);
+            return launch_pdl(k_blend_batch<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, s4, ft, image,
+                              t_final, n_contrib);
         case 32:
-            return launch_pdl(k_blend_batch<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, m4, conic, opacity,
-                              rgb, ft, image, t_final, n_contrib);
+            return launch_pdl(k_blend_batch<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, s4, ft, image,
+                              t_final, n_contrib);
         default:
             return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_backward_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
-                                  const float* sh, const FrameTable& ft, const float* mean2d, const float* conic,
-                                  const float* rgb, const float* opacity, const uint16_t* rect,
+                                  const float* sh, const FrameTable& ft, const float* splats, const uint16_t* rect,
                                   const uint32_t* offsets, const uint32_t* tiles_touched, const uint32_t* vals,
                                   const uint32_t* ranges, const float* t_final, const uint32_t* n_contrib,
                                   const float* d_image, float* d_means, float* d_log_scales, float* d_quats,
@@ -300,22 +281,22 @@ cudaError_t launch_backward_batch(int64_t n, const float* means, const float* lo
     float* partials = static_cast<float*>(scratch);
     const uint32_t ntiles = ft.tile_off[ft.views];
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
-    const float4* m4 = reinterpret_cast<const float4*>(mean2d);
+    const float4* s4 = reinterpret_cast<const float4*>(splats);
     const uint2* rc = reinterpret_cast<const uint2*>(rect);
     cudaError_t e = cudaSuccess;
     if (ntiles > 0) {
         switch (ft.f[0].TS) {
             case 8:
-                e = launch_pdl(k_blend_bwd_batch<8>, dim3(ntiles), dim3(64), 0, stream, r2, vals, n, m4, conic,
-                               opacity, rgb, rc, offsets, ft, t_final, n_contrib, d_image, partials);
+                e = launch_pdl(k_blend_bwd_batch<8>, dim3(ntiles), dim3(64), 0, stream, r2, vals, n, s4, rc, offsets,
+                               ft, t_final, n_contrib, d_image, partials);
                 break;
             case 16:
-                e = launch_pdl(k_blend_bwd_batch<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, m4, conic,
-                               opacity, rgb, rc, offsets, ft, t_final, n_contrib, d_image, partials);
+                e = launch_pdl(k_blend_bwd_batch<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, s4, rc,
+                               offsets, ft, t_final, n_contrib, d_image, partials);
                 break;
             case 32:
-                e = launch_pdl(k_blend_bwd_batch<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, m4, conic,
-                               opacity, rgb, rc, offsets, ft, t_final, n_contrib, d_image, partials);
+                e = launch_pdl(k_blend_bwd_batch<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, s4, rc,
+                               offsets, ft, t_final, n_contrib, d_image, partials);
                 break;
             default:
                 return cudaErrorInvalidValue;
@@ -325,8 +306,8 @@ cudaError_t launch_backward_batch(int64_t n, const float* means, const float* lo
     if (n > 0) {
         const int64_t blocks = (n + kBatchThreads - 1) / kBatchThreads;
         e = launch_pdl(k_preprocess_bwd_batch, dim3((unsigned)blocks), dim3(kBatchThreads), 0, stream, n, means,
-                       log_scales, reinterpret_cast<const float4*>(quats), reinterpret_cast<const float4*>(sh), ft, rgb,
-                       opacity, offsets, tiles_touched, (uint32_t)key_capacity, (const float*)partials, d_means,
+                       log_scales, reinterpret_cast<const float4*>(quats), reinterpret_cast<const float4*>(sh), ft, s4,
+                       offsets, tiles_touched, (uint32_t)key_capacity, (const float*)partials, d_means,
                        d_log_scales,
                        reinterpret_cast<float4*>(d_quats), d_logits, reinterpret_cast<float4*>(d_sh));
     }

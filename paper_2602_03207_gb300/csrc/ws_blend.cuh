@@ -2,6 +2,8 @@
 // single-view and the batched rasterisation kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "ws_common.cuh"
 
 namespace ws {
@@ -31,60 +33,90 @@ struct SplatRec {
     float4 col;   // r, g, b, -
 };
 
-// Per-splat inputs of the blend, read from the float outputs of
-// ws_preprocess: the double-float centre (made tile-relative without
-// large-magnitude rounding), the conic (a, b, c), sigma and the colour.
+// Per-splat inputs of the blend, read from the splat records of
+// ws_preprocess (three 16-byte loads of one 48-byte record): the double-float
+// centre (made tile-relative without large-magnitude rounding), the conic
+// (a, b, c), sigma and the colour.
 struct FloatSplats {
-    const float4* __restrict__ mean2d;
-    const float* __restrict__ conic;
-    const float* __restrict__ opacity;
-    const float* __restrict__ rgb;
+    const float4* __restrict__ rec;
     __device__ __forceinline__ void load(uint32_t g, float ox, float oy, float& x, float& y, float& a, float& b,
                                          float& c, float& op, float4& col) const {
-        const float4 m = __ldg(mean2d + g);
+        const float4 m = __ldg(rec + kSplatVec4 * g);
+        const float4 k = __ldg(rec + kSplatVec4 * g + 1);
+        col = __ldg(rec + kSplatVec4 * g + 2);
         x = __fadd_rn(__fsub_rn(m.x, ox), m.z);
         y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
-        a = __ldg(conic + 3 * g);
-        b = __ldg(conic + 3 * g + 1);
-        c = __ldg(conic + 3 * g + 2);
-        op = __ldg(opacity + g);
-        col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), 0.f);
+        a = k.x;
+        b = k.y;
+        c = k.z;
+        op = k.w;
     }
 };
 
+// Bitmask of a tile's 4x4 pixel sub-blocks (SPR per row and per column, bit
+// row * SPR + col) whose pixel centres meet the box [xl, xh] x [yl, yh].
+template <int SPR, typename MaskT>
+__device__ __forceinline__ MaskT box_subblock_mask(float xl, float xh, float yl, float yh) {
+    MaskT cols = 0;
+#pragma unroll
+    for (int c = 0; c < SPR; ++c)
+        cols |= (xl <= (float)(c * 4) + 3.5f && xh >= (float)(c * 4) + 0.5f) ? (MaskT(1) << c) : MaskT(0);
+    MaskT mask = 0;
+#pragma unroll
+    for (int r = 0; r < SPR; ++r)
+        mask |= (yl <= (float)(r * 4) + 3.5f && yh >= (float)(r * 4) + 0.5f) ? (cols << (r * SPR)) : MaskT(0);
+    return mask;
+}
+
+template <int SPR, typename MaskT>
+__device__ __forceinline__ MaskT splat_subblock_mask(float x, float y, float a, float b, float c, float qc) {
+    const float rdet = rcp_approx(fmaf(a, c, -b * b));
+    const float ex = sqrt_approx(qc * c * rdet) * 1.0001f + 1e-3f;
+    const float ey = sqrt_approx(qc * a * rdet) * 1.0001f + 1e-3f;
+    return box_subblock_mask<SPR, MaskT>(x - ex, x + ex, y - ey, y + ey);
+}
+
+template <int TS>
+struct SubMask {
+    using T = typename std::conditional<((TS / 4) * (TS / 4) > 32), unsigned long long, uint32_t>::type;
+};
+
 // One block per tile. Each warp owns WPB (TS^2/256, at least 1) 8x4 pixel
-// blocks. Splats are staged 256 at a time; while staging, every splat also
-// records the bitmask of the tile's 8x4 blocks that the bounding box of its
-// opacity-aware ellipse meets (splat_block_mask). Each warp then walks the
-// batch 32 splats at a time, ballots the bit of its own block and visits
-// only those splats, in list order, so per pixel the compositing order is
-// unchanged.
+// regions, each split into two 4x4 sub-blocks, one per half-warp. Splats are
+// staged 256 at a time; while staging, every splat also records the bitmask
+// of the tile's 4x4 sub-blocks that the bounding box of its opacity-aware
+// ellipse meets. Each half-warp then walks the batch 32 splats at a time and
+// visits only the splats of its own sub-block, in list order; the two halves
+// run in lockstep for max(visits of either half) steps, the idle half adding
+// w = 0, so per pixel the compositing order and arithmetic are unchanged.
 template <int TS, typename Splats>
 __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
                                            const Splats& sp, float* __restrict__ image, float* __restrict__ t_final,
                                            uint32_t* __restrict__ n_contrib) {
     constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
     constexpr int WARPS = THREADS / 32;
-    constexpr int PPT = TS * TS / THREADS;  // pixel blocks per warp (TS = 32: 4)
-    constexpr int BW = 8, BH = 4;           // warp pixel block
-    constexpr int BPR = TS / BW;            // blocks per row
-    constexpr int BROWS = TS / BH;          // block rows
-    static_assert(BPR * BROWS <= 32, "block mask is 32 bits");
+    constexpr int PPT = TS * TS / THREADS;  // 8x4 regions per warp (TS = 32: 4)
+    constexpr int RPR = TS / 8;             // regions per row
+    constexpr int SPR = TS / 4;             // sub-blocks per row
+    using MaskT = typename SubMask<TS>::T;
     __shared__ SplatRec s_rec[kBlendBatch];
-    __shared__ uint32_t s_mask[kBlendBatch];
+    __shared__ MaskT s_mask[kBlendBatch];
 
     const int tx = tile % f.TX, ty = tile / f.TX;
     const float ox = (float)(tx * TS), oy = (float)(ty * TS);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = lane >> 4;
 
     float px[PPT], py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
     uint32_t last[PPT];
+    int sba[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int b = warp + k * WARPS;
-        const int bx = (b % BPR) * BW, by = (b / BPR) * BH;
-        px[k] = (float)(bx + (lane & 7)) + 0.5f;
-        py[k] = (float)(by + (lane >> 3)) + 0.5f;
+        const int rg = warp + k * WARPS;
+        const int rx = rg % RPR, ry = rg / RPR;
+        px[k] = (float)(rx * 8 + half * 4 + (lane & 3)) + 0.5f;
+        py[k] = (float)(ry * 4 + ((lane >> 2) & 3)) + 0.5f;
+        sba[k] = ry * SPR + 2 * rx;
         T[k] = 1.f;
         C0[k] = C1[k] = C2[k] = 0.f;
         last[k] = 0;
@@ -104,25 +136,30 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
             r.geo2 = make_float4(-0.5f * kLog2e * c, L, 0.f, 0.f);
             s_rec[j] = r;
             const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, kTwoLn2 * (L - kLog2AlphaMin));
-            s_mask[j] = splat_block_mask<BW, BH, BPR, BROWS>(r.geo.x, r.geo.y, a, b, c, qc);
+            s_mask[j] = splat_subblock_mask<SPR, MaskT>(r.geo.x, r.geo.y, a, b, c, qc);
         }
         __syncthreads();
+        const uint32_t rel = start + 1 - range.x;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int blk = warp + k * WARPS;
             for (int base = 0; base < cnt; base += 32) {
                 const int jj = base + lane;
-                uint32_t bits = __ballot_sync(kFull, jj < cnt && ((s_mask[jj] >> blk) & 1u));
-                // Branch-free per splat: a skipped pair adds w = 0, which
-                // leaves C and T bit for bit unchanged.
-                while (bits) {
-                    const int j = base + __ffs(bits) - 1;
-                    bits &= bits - 1;
+                const MaskT m = jj < cnt ? s_mask[jj] : MaskT(0);
+                const uint32_t ba = __ballot_sync(kFull, (uint32_t)(m >> sba[k]) & 1u);
+                const uint32_t bb = __ballot_sync(kFull, (uint32_t)(m >> (sba[k] + 1)) & 1u);
+                uint32_t bits = half ? bb : ba;
+                const int steps = max(__popc(ba), __popc(bb));
+                for (int it = 0; it < steps; ++it) {
+                    // The idle half (no splat left) re-reads entry `base` and
+                    // adds w = 0, which leaves C and T bit for bit unchanged.
+                    const bool act = bits != 0u;
+                    const int j = base + (act ? __ffs(bits) - 1 : 0);
+                    bits &= bits - 1u;
                     const float4 geo = s_rec[j].geo;
                     const float2 geo2 = *reinterpret_cast<const float2*>(&s_rec[j].geo2);
                     const float dx = px[k] - geo.x, dy = py[k] - geo.y;
                     const float e = splat_log2_alpha(dx, dy, geo.z, geo.w, geo2.x, geo2.y);
-                    const bool keep = e >= kLog2AlphaMin;
+                    const bool keep = act && e >= kLog2AlphaMin;
                     const float alpha = fminf(kAlphaMax, ex2_approx(e));
                     const float w = keep ? alpha * T[k] : 0.f;
                     const float4 col = s_rec[j].col;
@@ -130,7 +167,7 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
                     C1[k] = fmaf(col.y, w, C1[k]);
                     C2[k] = fmaf(col.z, w, C2[k]);
                     T[k] = T[k] - w;
-                    last[k] = keep ? start + j + 1 - range.x : last[k];
+                    last[k] = keep ? rel + j : last[k];
                 }
             }
         }
@@ -165,9 +202,8 @@ struct BwdRec {
 // offsets[g * views + v] in a batch).
 template <int TS, typename SlotBase>
 __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
-                                               const float4* __restrict__ mean2d, const float* __restrict__ conic,
-                                               const float* __restrict__ opacity, const float* __restrict__ rgb,
-                                               const uint2* __restrict__ rect, SlotBase slot_of,
+                                               const float4* __restrict__ splats, const uint2* __restrict__ rect,
+                                               SlotBase slot_of,
                                                const float* __restrict__ t_final,
                                                const uint32_t* __restrict__ n_contrib,
                                                const float* __restrict__ d_image, float* __restrict__ partials) {
@@ -238,9 +274,10 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += THREADS) {
             const uint32_t g = __ldg(vals + range.x + lo + j);
-            const float4 m = __ldg(mean2d + g);
-            const float a = __ldg(conic + 3 * g), b = __ldg(conic + 3 * g + 1), c = __ldg(conic + 3 * g + 2);
-            const float op = __ldg(opacity + g);
+            const float4 m = __ldg(splats + kSplatVec4 * g);
+            const float4 k = __ldg(splats + kSplatVec4 * g + 1);
+            const float4 cl = __ldg(splats + kSplatVec4 * g + 2);
+            const float a = k.x, b = k.y, c = k.z, op = k.w;
             BwdRec r;
             r.geo.x = __fadd_rn(__fsub_rn(m.x, ox), m.z);
             r.geo.y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
@@ -248,7 +285,7 @@ __device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 r
             r.geo.w = -kLog2e * b;
             const float L = lg2_approx(op);
             r.geo2 = make_float4(-0.5f * kLog2e * c, L, a, b);
-            r.col = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), c);
+            r.col = make_float4(cl.x, cl.y, cl.z, c);
             s_rec[j] = r;
             const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, kTwoLn2 * (L - kLog2AlphaMin));
             s_mask[j] = splat_block_mask<BW, BH, BPR, BROWS>(r.geo.x, r.geo.y, a, b, c, qc);

@@ -15,6 +15,13 @@ constexpr uint32_t kFull = 0xffffffffu;
 // Bytes reserved at the head of every workspace for the status words.
 constexpr size_t kStatusBytes = 256;
 
+// Per-Gaussian splat record written by the pre-processing and read by the
+// blends (three float4: centre (x_hi, y_hi, x_lo, y_lo); conic a, b, c and
+// opacity sigma; colour r, g, b and a zero), so a gather of one splat touches
+// two 32-byte sectors instead of one per separate array.
+constexpr int kSplatFloats = 12;
+constexpr int kSplatVec4 = kSplatFloats / 4;
+
 // Camera and frame constants, derived on the host once per call and passed
 // by value to every kernel.
 struct Frame {

@@ -11,8 +11,7 @@ namespace ws {
 
 cudaError_t launch_preprocess(int64_t n, const float* means, const float* log_scales,
                               const float* quats, const float* logits, const float* sh,
-                              const Frame& f, float* mean2d, float* conic, float* depth,
-                              float* rgb, float* opacity, uint16_t* rect,
+                              const Frame& f, float* splats, float* depth, uint16_t* rect,
                               uint32_t* tiles_touched, cudaStream_t stream);
 
 // ---- compaction (scan of tiles_touched + key emission)
@@ -60,8 +59,7 @@ cudaError_t launch_sort_noalloc(const uint32_t* num_keys, int64_t key_capacity, 
 cudaError_t launch_tile_ranges(const uint64_t* keys, const uint32_t* num_keys, uint32_t* ranges, uint32_t ntiles,
                                cudaStream_t stream);
 cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t key_capacity_hint,
-                             const uint64_t* keys, const uint32_t* vals, const float* mean2d,
-                             const float* conic, const float* opacity, const float* rgb,
+                             const uint64_t* keys, const uint32_t* vals, const float* splats,
                              const Frame& f, uint32_t* ranges, float* image, float* t_final,
                              uint32_t* n_contrib, cudaStream_t stream);
 
@@ -80,8 +78,7 @@ struct QuadLayout {
     size_t sort, cull, dkeys, dkeys_alt, dvals, dvals_alt, offsets, quad, one, rect, zdepth, num_vis, ranges, total;
 };
 QuadLayout quad_layout(int64_t n, int64_t key_capacity, int64_t ntiles);
-cudaError_t launch_render_quads(int64_t n, const float* mean2d, const float* conic, const float* opacity,
-                                const float* rgb, const float* depth, const uint32_t* tiles_touched,
+cudaError_t launch_render_quads(int64_t n, const float* splats, const float* depth, const uint32_t* tiles_touched,
                                 const Frame& f, int64_t key_capacity, uint64_t* keys, uint32_t* vals,
                                 uint64_t* keys_alt, uint32_t* vals_alt, uint32_t* num_keys, float* image,
                                 float* t_final, void* workspace, cudaStream_t stream);
@@ -89,8 +86,7 @@ cudaError_t launch_render_quads(int64_t n, const float* mean2d, const float* con
 // ---- backward
 size_t backward_scratch_bytes(int64_t key_capacity);
 cudaError_t launch_backward(int64_t n, const float* means, const float* log_scales, const float* quats,
-                            const float* sh, const Frame& f, const float* mean2d, const float* conic,
-                            const float* rgb, const float* opacity, const uint16_t* rect,
+                            const float* sh, const Frame& f, const float* splats, const uint16_t* rect,
                             const uint32_t* offsets, const uint32_t* tiles_touched,
                             const uint32_t* vals, const uint32_t* ranges, const float* t_final,
                             const uint32_t* n_contrib, const float* d_image, float* d_means,
@@ -99,16 +95,13 @@ cudaError_t launch_backward(int64_t n, const float* means, const float* log_scal
 
 // ---- batched views (view-major per-(view, Gaussian) arrays)
 cudaError_t launch_preprocess_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
-                                    const float* logits, const float* sh, const FrameTable& ft, float* mean2d,
-                                    float* conic, float* depth, float* rgb, float* opacity, uint16_t* rect,
-                                    uint32_t* tiles_touched, cudaStream_t stream);
+                                    const float* logits, const float* sh, const FrameTable& ft, float* splats,
+                                    float* depth, uint16_t* rect, uint32_t* tiles_touched, cudaStream_t stream);
 cudaError_t launch_rasterize_batch(const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals, int64_t n,
-                                   const float* mean2d, const float* conic, const float* opacity, const float* rgb,
-                                   const FrameTable& ft, uint32_t* ranges, float* image, float* t_final,
+                                   const float* splats, const FrameTable& ft, uint32_t* ranges, float* image, float* t_final,
                                    uint32_t* n_contrib, cudaStream_t stream);
 cudaError_t launch_backward_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
-                                  const float* sh, const FrameTable& ft, const float* mean2d, const float* conic,
-                                  const float* rgb, const float* opacity, const uint16_t* rect,
+                                  const float* sh, const FrameTable& ft, const float* splats, const uint16_t* rect,
                                   const uint32_t* offsets, const uint32_t* tiles_touched, const uint32_t* vals,
                                   const uint32_t* ranges, const float* t_final, const uint32_t* n_contrib,
                                   const float* d_image, float* d_means, float* d_log_scales, float* d_quats,

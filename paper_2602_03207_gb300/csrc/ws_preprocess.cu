@@ -3,7 +3,8 @@
 //
 // One thread per Gaussian, 128-thread blocks. HBM-bound: 236 B of input per
 // visible Gaussian (59 floats), 16 B per opacity-culled one (logit, centre),
-// 44 B per one culled later (no SH); 60 B of output each. The 192-byte SH
+// 44 B per one culled later (no SH); 64 B of output each (the 48-byte splat
+// record, depth, rect, tile count). The 192-byte SH
 // record is the bulk of the traffic; each warp copies the SH of its
 // Gaussians that will probably be visible into shared memory with
 // asynchronous, coalesced 16-byte copies issued before the projection math
@@ -23,10 +24,8 @@ constexpr int kPreThreads = 128;
 __global__ void __launch_bounds__(kPreThreads)
 k_preprocess(int64_t n, const float* __restrict__ means, const float* __restrict__ log_scales,
              const float4* __restrict__ quats, const float* __restrict__ logits,
-             const float4* __restrict__ sh, const Frame f, float4* __restrict__ mean2d,
-             float* __restrict__ conic, float* __restrict__ depth, float* __restrict__ rgb,
-             float* __restrict__ opacity, uint2* __restrict__ rect,
-             uint32_t* __restrict__ tiles_touched) {
+             const float4* __restrict__ sh, const Frame f, float4* __restrict__ splats,
+             float* __restrict__ depth, uint2* __restrict__ rect, uint32_t* __restrict__ tiles_touched) {
     __shared__ __align__(16) float s_sh[kPreThreads / kWarp][kWarp * kShPad];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
@@ -100,14 +99,7 @@ k_preprocess(int64_t n, const float* __restrict__ means, const float* __restrict
     // warp writes whole 32-byte sectors: a sector left partly written would
     // cost a read of it from DRAM when it leaves the L2.
     if (valid) {
-        mean2d[i] = vis ? P.m4 : make_float4(0.f, 0.f, 0.f, 0.f);
-        conic[3 * i] = vis ? P.ca : 0.f;
-        conic[3 * i + 1] = vis ? P.cb : 0.f;
-        conic[3 * i + 2] = vis ? P.cc : 0.f;
-        rgb[3 * i] = c3.x;
-        rgb[3 * i + 1] = c3.y;
-        rgb[3 * i + 2] = c3.z;
-        opacity[i] = vis ? P.sigma : 0.f;
+        store_splat(splats + kSplatVec4 * i, vis, P, c3);
         rect[i] = vis ? make_uint2(P.x0 | (P.y0 << 16), P.x1 | (P.y1 << 16)) : make_uint2(0u, 0u);
         tiles_touched[i] = vis ? (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1) : 0u;
     }
@@ -117,15 +109,13 @@ k_preprocess(int64_t n, const float* __restrict__ means, const float* __restrict
 
 cudaError_t launch_preprocess(int64_t n, const float* means, const float* log_scales,
                               const float* quats, const float* logits, const float* sh,
-                              const Frame& f, float* mean2d, float* conic, float* depth,
-                              float* rgb, float* opacity, uint16_t* rect,
+                              const Frame& f, float* splats, float* depth, uint16_t* rect,
                               uint32_t* tiles_touched, cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
     const int64_t blocks = (n + kPreThreads - 1) / kPreThreads;
     return launch_pdl(k_preprocess, dim3((unsigned)blocks), dim3(kPreThreads), 0, stream, n, means, log_scales,
                       reinterpret_cast<const float4*>(quats), logits, reinterpret_cast<const float4*>(sh), f,
-                      reinterpret_cast<float4*>(mean2d), conic, depth, rgb, opacity,
-                      reinterpret_cast<uint2*>(rect), tiles_touched);
+                      reinterpret_cast<float4*>(splats), depth, reinterpret_cast<uint2*>(rect), tiles_touched);
 }
 
 }  // namespace ws

@@ -95,6 +95,14 @@ struct Projection {
     uint32_t x0, y0, x1, y1;  // tile rectangle (inclusive)
 };
 
+// Stores the splat record of one Gaussian (zeros when it is not visible).
+__device__ __forceinline__ void store_splat(float4* __restrict__ dst, bool vis, const Projection& P, float3 c3) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    dst[0] = vis ? P.m4 : z;
+    dst[1] = vis ? make_float4(P.ca, P.cb, P.cc, P.sigma) : z;
+    dst[2] = make_float4(c3.x, c3.y, c3.z, 0.f);
+}
+
 // Projection of one Gaussian that passed the opacity and near-plane tests:
 // Sigma = M M^T with M = R(q) diag(exp(log_scale)) (§2.1); the centre through
 // the pinhole in double-float; Sigma' = V V^T + dilation I with V = J W M

@@ -41,8 +41,7 @@ struct QuadRec {
 // Also writes the per-Gaussian items of the compaction: one "tile" (0) per
 // visible splat, so the emission produces (depth bits, index) in index order.
 __global__ void __launch_bounds__(kQuadThreads)
-k_quad_setup(int64_t n, const float* __restrict__ conic, const float* __restrict__ opacity,
-             const uint32_t* __restrict__ tiles_touched, const Frame f, QuadRec* __restrict__ quad,
+k_quad_setup(int64_t n, const float4* __restrict__ splats, const uint32_t* __restrict__ tiles_touched, const Frame f, QuadRec* __restrict__ quad,
              uint32_t* __restrict__ one, uint2* __restrict__ rect0) {
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * kQuadThreads + threadIdx.x;
@@ -51,8 +50,8 @@ k_quad_setup(int64_t n, const float* __restrict__ conic, const float* __restrict
     one[i] = vis ? 1u : 0u;
     rect0[i] = make_uint2(0u, 0u);
     if (!vis) return;
-    const float a = __ldg(conic + 3 * i), b = __ldg(conic + 3 * i + 1), c = __ldg(conic + 3 * i + 2);
-    const float sigma = __ldg(opacity + i);
+    const float4 k4 = __ldg(splats + kSplatVec4 * i + 1);
+    const float a = k4.x, b = k4.y, c = k4.z, sigma = k4.w;
     const float m = 0.5f * (a + c), h = 0.5f * (a - c);
     const float d = sqrtf(fmaf(h, h, b * b));
     const float mu2 = m + d;                         // larger eigenvalue: the minor axis
@@ -92,7 +91,7 @@ k_quad_setup(int64_t n, const float* __restrict__ conic, const float* __restrict
 // the emission writes (tile << 31, rank) pairs in rank order.
 __global__ void __launch_bounds__(kQuadThreads)
 k_quad_bin_items(int64_t n, const uint32_t* __restrict__ num_vis, const uint32_t* __restrict__ order,
-                 const float4* __restrict__ mean2d, const QuadRec* __restrict__ quad, const Frame f,
+                 const float4* __restrict__ splats, const QuadRec* __restrict__ quad, const Frame f,
                  uint32_t* __restrict__ touched, uint2* __restrict__ rect, float* __restrict__ zero_depth) {
     pdl_wait();
     const int64_t k = (int64_t)blockIdx.x * kQuadThreads + threadIdx.x;
@@ -103,7 +102,7 @@ k_quad_bin_items(int64_t n, const uint32_t* __restrict__ num_vis, const uint32_t
         return;
     }
     const uint32_t g = __ldg(order + k);
-    const float4 m = __ldg(mean2d + g);
+    const float4 m = __ldg(splats + kSplatVec4 * g);
     const QuadRec q = quad[g];
     const float cx = m.x + m.z, cy = m.y + m.w;
     const float its = 1.f / (float)f.TS;
@@ -134,9 +133,8 @@ struct QuadStage {
 template <int TS>
 __global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS)
 k_blend_quads(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ranks,
-              const uint32_t* __restrict__ order, const float4* __restrict__ mean2d,
-              const QuadRec* __restrict__ quad, const float* __restrict__ opacity, const float* __restrict__ rgb,
-              const Frame f, float* __restrict__ image, float* __restrict__ t_final) {
+              const uint32_t* __restrict__ order, const float4* __restrict__ splats,
+              const QuadRec* __restrict__ quad, const Frame f, float* __restrict__ image, float* __restrict__ t_final) {
     constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
     constexpr int WARPS = THREADS / 32;
     constexpr int PPT = TS * TS / THREADS;
@@ -167,7 +165,9 @@ k_blend_quads(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ran
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += THREADS) {
             const uint32_t g = __ldg(order + __ldg(ranks + range.x + lo + j));
-            const float4 m = __ldg(mean2d + g);
+            const float4 m = __ldg(splats + kSplatVec4 * g);
+            const float op = __ldg(splats + kSplatVec4 * g + 1).w;
+            const float4 cl = __ldg(splats + kSplatVec4 * g + 2);
             const QuadRec q = quad[g];
             QuadStage st;
             st.cx = __fadd_rn(__fsub_rn(m.x, ox), m.z);
@@ -177,10 +177,10 @@ k_blend_quads(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ran
             st.m10 = q.m10;
             st.m11 = q.m11;
             st.r = q.r;
-            st.l2s = log2f(__ldg(opacity + g));
-            st.cr = __ldg(rgb + 3 * g);
-            st.cg = __ldg(rgb + 3 * g + 1);
-            st.cb = __ldg(rgb + 3 * g + 2);
+            st.l2s = log2f(op);
+            st.cr = cl.x;
+            st.cg = cl.y;
+            st.cb = cl.z;
             st.pad = 0.f;
             s_q[j] = st;
             s_mask[j] = box_block_mask<BW, BH, BPR, BROWS>(st.cx - q.hx, st.cx + q.hx, st.cy - q.hy, st.cy + q.hy);
@@ -254,8 +254,7 @@ QuadLayout quad_layout(int64_t n, int64_t key_capacity, int64_t ntiles) {
     return L;
 }
 
-cudaError_t launch_render_quads(int64_t n, const float* mean2d, const float* conic, const float* opacity,
-                                const float* rgb, const float* depth, const uint32_t* tiles_touched,
+cudaError_t launch_render_quads(int64_t n, const float* splats, const float* depth, const uint32_t* tiles_touched,
                                 const Frame& f, int64_t key_capacity, uint64_t* keys, uint32_t* vals,
                                 uint64_t* keys_alt, uint32_t* vals_alt, uint32_t* num_keys, float* image,
                                 float* t_final, void* workspace, cudaStream_t stream) {
@@ -274,13 +273,14 @@ cudaError_t launch_render_quads(int64_t n, const float* mean2d, const float* con
     float* zdepth = reinterpret_cast<float*>(w + L.zdepth);
     uint32_t* num_vis = reinterpret_cast<uint32_t*>(w + L.num_vis);
     uint2* ranges = reinterpret_cast<uint2*>(w + L.ranges);
+    const float4* s4 = reinterpret_cast<const float4*>(splats);
     const dim3 grid_n((unsigned)((n + kQuadThreads - 1) / kQuadThreads > 0 ? (n + kQuadThreads - 1) / kQuadThreads
                                                                                : 1));
     cudaError_t e;
     // 1. quads, and the compaction of the visible splats into (depth, index)
     if (n > 0) {
-        e = launch_pdl(k_quad_setup, grid_n, dim3(kQuadThreads), 0, stream, n, conic, opacity, tiles_touched, f,
-                       quad, one, rect);
+        e = launch_pdl(k_quad_setup, grid_n, dim3(kQuadThreads), 0, stream, n, s4, tiles_touched, f, quad, one,
+                       rect);
         if (e != cudaSuccess) return e;
     }
     e = launch_cull(n, one, reinterpret_cast<const uint16_t*>(rect), depth, f, offsets, dkeys, dvals, n, num_vis,
@@ -294,7 +294,7 @@ cudaError_t launch_render_quads(int64_t n, const float* mean2d, const float* con
     // 3. binning in depth order, then a stable partition by tile
     if (n > 0) {
         e = launch_pdl(k_quad_bin_items, grid_n, dim3(kQuadThreads), 0, stream, n, (const uint32_t*)num_vis, order,
-                       reinterpret_cast<const float4*>(mean2d), (const QuadRec*)quad, f, one, rect, zdepth);
+                       s4, (const QuadRec*)quad, f, one, rect, zdepth);
         if (e != cudaSuccess) return e;
     }
     e = launch_cull(n, one, reinterpret_cast<const uint16_t*>(rect), zdepth, f, offsets, keys, vals, key_capacity,
@@ -311,17 +311,16 @@ cudaError_t launch_render_quads(int64_t n, const float* mean2d, const float* con
     e = launch_tile_ranges(pk, num_keys, reinterpret_cast<uint32_t*>(ranges), (uint32_t)ntiles, stream);
     if (e != cudaSuccess) return e;
     // 4. back-to-front quads per tile
-    const float4* m4 = reinterpret_cast<const float4*>(mean2d);
     switch (f.TS) {
         case 8:
             return launch_pdl(k_blend_quads<8>, dim3((unsigned)ntiles), dim3(64), 0, stream, (const uint2*)ranges, pv,
-                              order, m4, (const QuadRec*)quad, opacity, rgb, f, image, t_final);
+                              order, s4, (const QuadRec*)quad, f, image, t_final);
         case 16:
             return launch_pdl(k_blend_quads<16>, dim3((unsigned)ntiles), dim3(256), 0, stream, (const uint2*)ranges,
-                              pv, order, m4, (const QuadRec*)quad, opacity, rgb, f, image, t_final);
+                              pv, order, s4, (const QuadRec*)quad, f, image, t_final);
         case 32:
             return launch_pdl(k_blend_quads<32>, dim3((unsigned)ntiles), dim3(256), 0, stream, (const uint2*)ranges,
-                              pv, order, m4, (const QuadRec*)quad, opacity, rgb, f, image, t_final);
+                              pv, order, s4, (const QuadRec*)quad, f, image, t_final);
         default:
             return cudaErrorInvalidValue;
     }

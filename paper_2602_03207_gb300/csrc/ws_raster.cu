@@ -6,14 +6,14 @@
 // centre - splat centre; a < 1/255 is skipped; C += c a T; T *= 1 - a.
 //
 // The splats of a tile are staged through shared memory in batches of 256:
-// each thread gathers one splat (value -> Gaussian index -> centre, conic,
-// opacity, colour), converts its centre to tile-relative coordinates with
-// the double-float centre (so pixel offsets carry no large-magnitude
-// rounding), folds -log2(e)/2 into the conic so the exponent is one ex2
-// instruction, and computes the box of its opacity-aware extent (§3.4).
-// A warp covers an 8x4 pixel block; a splat whose box misses the block is
-// skipped by the whole warp at once (a warp-uniform branch), which removes
-// most of the evaluations of small splats that only graze a tile.
+// each thread gathers one splat record (value -> Gaussian index -> its
+// 48-byte record: centre, conic, opacity, colour), converts its centre to
+// tile-relative coordinates with the double-float centre (so pixel offsets
+// carry no large-magnitude rounding), folds -log2(e)/2 into the conic so the
+// exponent is one ex2 instruction, and computes the box of its
+// opacity-aware extent (§3.4). A half-warp covers a 4x4 pixel sub-block; a
+// splat whose box misses the sub-block is skipped by that half-warp, which
+// removes most of the evaluations of small splats that only graze a tile.
 //
 // FP32-pipe + SFU bound: ~17 FP32 instructions and one ex2 per evaluated
 // (pixel, splat) pair.
@@ -50,12 +50,10 @@ k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ nu
 
 template <int TS>
 __global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS)
-k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-        const float4* __restrict__ mean2d, const float* __restrict__ conic,
-        const float* __restrict__ opacity, const float* __restrict__ rgb, const Frame f,
-        float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
+k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, const float4* __restrict__ splats,
+        const Frame f, float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
     pdl_wait();
-    const FloatSplats sp{mean2d, conic, opacity, rgb};
+    const FloatSplats sp{splats};
     blend_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, sp, image, t_final, n_contrib);
 }
 
@@ -71,8 +69,7 @@ cudaError_t launch_tile_ranges(const uint64_t* keys, const uint32_t* num_keys, u
 }
 
 cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t /*key_capacity_hint*/,
-                             const uint64_t* keys, const uint32_t* vals, const float* mean2d,
-                             const float* conic, const float* opacity, const float* rgb,
+                             const uint64_t* keys, const uint32_t* vals, const float* splats,
                              const Frame& f, uint32_t* ranges, float* image, float* t_final,
                              uint32_t* n_contrib, cudaStream_t stream) {
     const int ntiles = f.TX * f.TY;
@@ -80,17 +77,17 @@ cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t /*key_capacity_hi
     cudaError_t e = launch_tile_ranges(keys, num_keys, ranges, (uint32_t)ntiles, stream);
     if (e != cudaSuccess) return e;
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
-    const float4* m4 = reinterpret_cast<const float4*>(mean2d);
+    const float4* s4 = reinterpret_cast<const float4*>(splats);
     switch (f.TS) {
         case 8:
-            return launch_pdl(k_blend<8>, dim3(ntiles), dim3(64), 0, stream, r2, vals, m4, conic, opacity, rgb, f,
-                              image, t_final, n_contrib);
+            return launch_pdl(k_blend<8>, dim3(ntiles), dim3(64), 0, stream, r2, vals, s4, f, image, t_final,
+                              n_contrib);
         case 16:
-            return launch_pdl(k_blend<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, m4, conic, opacity, rgb,
-                              f, image, t_final, n_contrib);
+            return launch_pdl(k_blend<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, s4, f, image, t_final,
+                              n_contrib);
         case 32:
-            return launch_pdl(k_blend<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, m4, conic, opacity, rgb,
-                              f, image, t_final, n_contrib);
+            return launch_pdl(k_blend<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, s4, f, image, t_final,
+                              n_contrib);
         default:
             return cudaErrorInvalidValue;
     }

@@ -63,11 +63,8 @@ class Renderer:
         d = torch.device(device)
         n1 = max(self.n, 1)
         cap = max(self.key_capacity, 1)
-        self.mean2d = torch.empty((n1, 4), dtype=torch.float32, device=d)
-        self.conic = torch.empty((n1, 3), dtype=torch.float32, device=d)
+        self.splats = torch.empty((n1, capi.WS_SPLAT_FLOATS), dtype=torch.float32, device=d)
         self.depth = torch.empty(n1, dtype=torch.float32, device=d)
-        self.rgb = torch.empty((n1, 3), dtype=torch.float32, device=d)
-        self.opacity = torch.empty(n1, dtype=torch.float32, device=d)
         self.rect = torch.empty((n1, 4), dtype=torch.int16, device=d)       # uint16 payload
         self.tiles_touched = torch.empty(n1, dtype=torch.int32, device=d)   # uint32 payload
         self.offsets = torch.empty(self.n + 1, dtype=torch.int32, device=d)
@@ -97,6 +94,23 @@ class Renderer:
                 raise ValueError("ws_workspace_bytes rejected the configuration")
             self.workspace = torch.zeros(nbytes, dtype=torch.uint8, device=self.image.device)
 
+    # views of the splat record (centre hi/lo, conic, sigma, colour)
+    @property
+    def mean2d(self):
+        return self.splats[:, 0:4]
+
+    @property
+    def conic(self):
+        return self.splats[:, 4:7]
+
+    @property
+    def opacity(self):
+        return self.splats[:, 7]
+
+    @property
+    def rgb(self):
+        return self.splats[:, 8:11]
+
     # ------------------------------------------------------------ stages
     def preprocess(self, scene, cam, stream=None):
         if self.packed:
@@ -105,8 +119,8 @@ class Renderer:
                                       self.axes, self.rgba, self.depth, self.rect, self.tiles_touched, stream)
             return
         capi.ws_preprocess(self.n, scene["means"], scene["log_scales"], scene["quats"],
-                           scene["opacity_logits"], scene["sh"], cam, self.cfg, self.mean2d, self.conic,
-                           self.depth, self.rgb, self.opacity, self.rect, self.tiles_touched, stream)
+                           scene["opacity_logits"], scene["sh"], cam, self.cfg, self.splats, self.depth, self.rect,
+                           self.tiles_touched, stream)
 
     def cull(self, cam, stream=None):
         self._ensure_workspace(cam)
@@ -132,9 +146,8 @@ class Renderer:
                                      self.rgba, cam, self.cfg, self.ranges, self.image, self.t_final,
                                      self.n_contrib, stream)
             return
-        capi.ws_rasterize(self.num_keys, self.sorted_keys, self.sorted_vals, self.mean2d, self.conic,
-                          self.opacity, self.rgb, cam, self.cfg, self.ranges, self.image, self.t_final,
-                          self.n_contrib, stream)
+        capi.ws_rasterize(self.num_keys, self.sorted_keys, self.sorted_vals, self.splats, cam, self.cfg,
+                          self.ranges, self.image, self.t_final, self.n_contrib, stream)
 
     def forward(self, scene, cam_dict, stream=None):
         """One frame; returns the image tensor (H, W, 3). Asynchronous."""
@@ -160,10 +173,9 @@ class Renderer:
             if nbytes == 0:
                 raise ValueError("ws_quads_workspace_bytes rejected the configuration")
             self.quad_workspace = torch.zeros(nbytes, dtype=torch.uint8, device=self.image.device)
-        capi.ws_render_quads(self.n, self.mean2d, self.conic, self.opacity, self.rgb, self.depth,
-                             self.tiles_touched, cam, self.cfg, self.key_capacity, self.keys, self.vals,
-                             self.keys_alt, self.vals_alt, self.num_keys, self.image, self.t_final,
-                             self.quad_workspace, stream)
+        capi.ws_render_quads(self.n, self.splats, self.depth, self.tiles_touched, cam, self.cfg,
+                             self.key_capacity, self.keys, self.vals, self.keys_alt, self.vals_alt, self.num_keys,
+                             self.image, self.t_final, self.quad_workspace, stream)
         return self.image
 
     def check_quads_status(self, stream=None):
@@ -188,8 +200,8 @@ class Renderer:
              "sh": torch.empty((n1, 16, 3), dtype=torch.float32, device=d)}
         d_image = d_image.contiguous()
         capi.ws_rasterize_backward(self.n, scene["means"], scene["log_scales"], scene["quats"],
-                                   scene["opacity_logits"], scene["sh"], cam, self.cfg, self.mean2d, self.conic,
-                                   self.rgb, self.opacity, self.rect, self.offsets, self.tiles_touched,
+                                   scene["opacity_logits"], scene["sh"], cam, self.cfg, self.splats, self.rect,
+                                   self.offsets, self.tiles_touched,
                                    self.sorted_vals, self.ranges, self.t_final, self.n_contrib, d_image,
                                    self.key_capacity, g["means"], g["log_scales"], g["quats"],
                                    g["opacity_logits"], g["sh"], self.workspace, stream)

@@ -38,7 +38,8 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.ws_abi_version() == 1
+    from paper_2602_03207_gb300 import capi
+    assert lib.ws_abi_version() == capi.WS_ABI_VERSION == 2
     assert lib.ws_status_string(0) == b"ok"
     assert lib.ws_status_string(3) == b"key capacity exceeded"
 
@@ -60,15 +61,14 @@ def test_workspace_and_argument_checks(lib):
     assert capi.ws_workspace_bytes(10, 10, cam0, cfg) == 0
     # synchronous argument errors (returned before any launch)
     st = lib.ws_preprocess(-1, None, None, None, None, None, C.byref(cam), C.byref(cfg),
-                           None, None, None, None, None, None, None, None)
+                           None, None, None, None, None)
     assert st == capi.WS_ERR_INVALID_ARG
     st = lib.ws_preprocess(10, None, None, None, None, None, C.byref(cam), C.byref(cfg),
-                           None, None, None, None, None, None, None, None)
+                           None, None, None, None, None)
     assert st == capi.WS_ERR_INVALID_ARG
     misaligned = C.c_void_p(0x1004)
     st = lib.ws_preprocess(10, misaligned, misaligned, misaligned, misaligned, misaligned, C.byref(cam),
-                           C.byref(cfg), misaligned, misaligned, misaligned, misaligned, misaligned,
-                           misaligned, misaligned, None)
+                           C.byref(cfg), misaligned, misaligned, misaligned, misaligned, None)
     assert st == capi.WS_ERR_INVALID_ARG
     in_alt = C.c_int32(0)
     st = lib.ws_sort(None, 10, 0, 65, None, None, None, None, C.byref(cfg), None, C.byref(in_alt), None)

@@ -128,8 +128,9 @@ def test_ragged_resolution_and_background():
 
 
 def test_culled_entries_are_written_as_zeros():
-    """Every output entry is written: a culled Gaussian's mean2d, conic, rgb,
-    opacity and rect are zeros, whatever the buffers held before."""
+    """Every output entry is written: a culled Gaussian's splat record (centre,
+    conic, opacity, colour) and rect are zeros, and every record's padding
+    word is zero, whatever the buffers held before."""
     import torch
     from paper_2602_03207_gb300 import render
     scene, cam = S.small_forward()
@@ -138,8 +139,7 @@ def test_culled_entries_are_written_as_zeros():
     scene["opacity_logits"][::3] = -7.0  # below 1/255: culled
     n = scene["means"].shape[0]
     r = render.Renderer(n, cam["width"], cam["height"])
-    for t in (r.mean2d, r.conic, r.rgb, r.opacity):
-        t.fill_(float("nan"))
+    r.splats.fill_(float("nan"))
     r.rect.fill_(-1)
     r.preprocess(render.scene_to_device(scene), capi_camera(cam))
     torch.cuda.synchronize()
@@ -152,6 +152,7 @@ def test_culled_entries_are_written_as_zeros():
     for k in ("mean2d4", "conic", "rgb", "opacity", "rect"):
         np.testing.assert_array_equal(g[k][culled], 0)
         assert np.isfinite(g[k][~culled].astype(np.float64)).all(), k
+    np.testing.assert_array_equal(r.splats[:n, 11].cpu().numpy(), 0)
 
 
 def test_empty_and_fully_culled_scenes():
