@@ -101,6 +101,7 @@ typedef struct ws_config {
 #define WS_CFG_SORT_LOOKBACK 4u   /* ws_sort: single-sweep decoupled look-back variant */
 #define WS_CFG_FIXED_RADIUS 8u    /* ablation: every splat's box as at sigma = 1 (no opacity-aware extent) */
 #define WS_CFG_SORT_SEGMENTED 16u /* ws_sort: partition by bits [31, end) then sort each segment on chip */
+#define WS_CFG_PERSISTENT 32u     /* ws_render_train_l2_batch: one persistent grid over every (view, tile) */
 
 /* Library ABI version (WS_ABI_VERSION of the build). */
 int32_t ws_abi_version(void);
@@ -384,6 +385,43 @@ ws_status ws_rasterize_backward_batch(int64_t n, const float *means, const float
                                       int64_t key_capacity, float *d_means, float *d_log_scales,
                                       float *d_quats, float *d_opacity_logits, float *d_sh,
                                       void *workspace, void *stream);
+
+/* One training step of the L2 loss L = 1/2 ||image - target||^2 after
+ * ws_preprocess, ws_cull and ws_sort: the work of ws_rasterize,
+ * ws_image_residual and ws_rasterize_backward in two launches. A first kernel
+ * takes each tile once: it composites the tile (the image, t_final and
+ * n_contrib of ws_rasterize, bit for bit), forms d = image - target for its
+ * pixels in registers, and walks the same list back to front writing each
+ * pair's partial derivatives to its emission slot (reusing the staged splat
+ * records when the tile's list fits one batch of 256); a second sums each
+ * Gaussian's records in slot order and applies the pre-processing adjoint.
+ * Arguments are those of the three calls it replaces (target (device)
+ * [H][W][3]); the gradients equal ws_rasterize_backward's for d_image =
+ * image - target bit for bit. The paper has no training step; this fusion
+ * has no counterpart there. Errors as ws_rasterize_backward. */
+ws_status ws_render_train_l2(int64_t n, const float *means, const float *log_scales, const float *quats,
+                             const float *sh, const ws_camera *cam, const ws_config *cfg, const uint32_t *num_keys,
+                             const uint64_t *keys, const uint32_t *vals, const float *splats, const uint16_t *rect,
+                             const uint32_t *offsets, const uint32_t *tiles_touched, const float *target,
+                             int64_t key_capacity, uint32_t *ranges, float *image, float *t_final,
+                             uint32_t *n_contrib, float *d_means, float *d_log_scales, float *d_quats,
+                             float *d_opacity_logits, float *d_sh, void *workspace, void *stream);
+
+/* ws_render_train_l2 over a batch of views (the layouts of the batched calls
+ * above; target packed like the images), gradients summed over the views in
+ * view order. With cfg->flags & WS_CFG_PERSISTENT the per-tile kernel is one
+ * persistent grid, as many blocks as fit on the GPU at once, block b taking
+ * the (view, tile) items b, b + G, b + 2G, ... of the global tile numbering
+ * (a static assignment; no block waits on another); otherwise one block per
+ * item. Both give the same results bit for bit. */
+ws_status ws_render_train_l2_batch(int64_t n, const float *means, const float *log_scales, const float *quats,
+                                   const float *sh, int32_t views, const ws_camera *cams, const ws_config *cfg,
+                                   const uint32_t *num_keys, const uint64_t *keys, const uint32_t *vals,
+                                   const float *splats, const uint16_t *rect, const uint32_t *offsets,
+                                   const uint32_t *tiles_touched, const float *target, int64_t key_capacity,
+                                   uint32_t *ranges, float *image, float *t_final, uint32_t *n_contrib,
+                                   float *d_means, float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                                   float *d_sh, void *workspace, void *stream);
 
 /* d_image = image - target over `count` floats (device): the gradient of the
  * L2 loss 1/2 ||image - target||^2 used by the training step. */

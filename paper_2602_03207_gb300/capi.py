@@ -24,6 +24,7 @@ WS_OK, WS_ERR_INVALID_ARG, WS_ERR_CUDA, WS_ERR_CAPACITY, WS_ERR_TIMEOUT, WS_ERR_
 WS_FLAG_CAPACITY, WS_FLAG_TIMEOUT = 1, 2
 WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL, WS_CFG_SORT_LOOKBACK, WS_CFG_FIXED_RADIUS = 1, 2, 4, 8
 WS_CFG_SORT_SEGMENTED = 16
+WS_CFG_PERSISTENT = 32
 WS_ABI_VERSION = 2
 WS_SPLAT_FLOATS = 12  # floats per splat record: centre hi/lo (4), conic (3), sigma, colour (3), 0
 
@@ -31,7 +32,7 @@ EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_prepr
            "ws_sort", "ws_sort_noalloc", "ws_sort_noalloc_max_keys", "ws_rasterize",
            "ws_rasterize_backward", "ws_read_status", "ws_batch_max_views", "ws_batch_workspace_bytes",
            "ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
-           "ws_image_residual", "ws_sort_test_stalled_tile")
+           "ws_image_residual", "ws_sort_test_stalled_tile", "ws_render_train_l2", "ws_render_train_l2_batch")
 
 
 class WsError(RuntimeError):
@@ -112,8 +113,13 @@ def lib():
             L.ws_rasterize_backward_batch.argtypes = [I64, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P,
                                                       P, P, P, P, I64, P, P, P, P, P, P, P]
             L.ws_image_residual.argtypes = [I64, P, P, P, P]
+            L.ws_render_train_l2.argtypes = [I64, P, P, P, P, cam_p, cfg_p, P, P, P, P, P, P, P, P, I64, P, P, P, P,
+                                             P, P, P, P, P, P, P]
+            L.ws_render_train_l2_batch.argtypes = [I64, P, P, P, P, I32, cam_p, cfg_p, P, P, P, P, P, P, P, P, I64,
+                                                   P, P, P, P, P, P, P, P, P, P, P]
             for name in ("ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
-                         "ws_image_residual", "ws_sort_test_stalled_tile"):
+                         "ws_image_residual", "ws_sort_test_stalled_tile", "ws_render_train_l2",
+                         "ws_render_train_l2_batch"):
                 getattr(L, name).restype = I32
             for name in ("ws_preprocess", "ws_cull", "ws_sort", "ws_rasterize", "ws_rasterize_backward",
                          "ws_read_status"):
@@ -298,3 +304,23 @@ def ws_rasterize_backward_batch(n, means, log_scales, quats, sh, cams_arr, cfg, 
 def ws_image_residual(count, image, target, d_image, stream=None):
     _check("ws_image_residual", lib().ws_image_residual(int(count), _ptr(image), _ptr(target), _ptr(d_image),
                                                         _stream(stream)))
+
+
+def ws_render_train_l2(n, means, log_scales, quats, sh, cam, cfg, num_keys, keys, vals, splats, rect, offsets,
+                       tiles_touched, target, key_capacity, ranges, image, t_final, n_contrib, d_means, d_log_scales,
+                       d_quats, d_opacity_logits, d_sh, workspace, stream=None):
+    _check("ws_render_train_l2", lib().ws_render_train_l2(
+        int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(sh), C.byref(cam), C.byref(cfg), _ptr(num_keys),
+        _ptr(keys), _ptr(vals), _ptr(splats), _ptr(rect), _ptr(offsets), _ptr(tiles_touched), _ptr(target),
+        int(key_capacity), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib), _ptr(d_means),
+        _ptr(d_log_scales), _ptr(d_quats), _ptr(d_opacity_logits), _ptr(d_sh), _ptr(workspace), _stream(stream)))
+
+
+def ws_render_train_l2_batch(n, means, log_scales, quats, sh, cams_arr, cfg, num_keys, keys, vals, splats, rect,
+                             offsets, tiles_touched, target, key_capacity, ranges, image, t_final, n_contrib, d_means,
+                             d_log_scales, d_quats, d_opacity_logits, d_sh, workspace, stream=None):
+    _check("ws_render_train_l2_batch", lib().ws_render_train_l2_batch(
+        int(n), _ptr(means), _ptr(log_scales), _ptr(quats), _ptr(sh), len(cams_arr), cams_arr, C.byref(cfg),
+        _ptr(num_keys), _ptr(keys), _ptr(vals), _ptr(splats), _ptr(rect), _ptr(offsets), _ptr(tiles_touched),
+        _ptr(target), int(key_capacity), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib), _ptr(d_means),
+        _ptr(d_log_scales), _ptr(d_quats), _ptr(d_opacity_logits), _ptr(d_sh), _ptr(workspace), _stream(stream)))

@@ -457,6 +457,63 @@ ws_status ws_rasterize_backward_batch(int64_t n, const float* means, const float
                                                  static_cast<cudaStream_t>(stream)));
 }
 
+ws_status ws_render_train_l2(int64_t n, const float* means, const float* log_scales, const float* quats,
+                             const float* sh, const ws_camera* cam, const ws_config* cfg, const uint32_t* num_keys,
+                             const uint64_t* keys, const uint32_t* vals, const float* splats, const uint16_t* rect,
+                             const uint32_t* offsets, const uint32_t* tiles_touched, const float* target,
+                             int64_t key_capacity, uint32_t* ranges, float* image, float* t_final,
+                             uint32_t* n_contrib, float* d_means, float* d_log_scales, float* d_quats,
+                             float* d_opacity_logits, float* d_sh, void* workspace, void* stream) {
+    if (n < 0 || n >= (int64_t(1) << 32) || key_capacity < 0 || key_capacity >= (int64_t(1) << 31))
+        return WS_ERR_INVALID_ARG;
+    if (!valid_camera(cam) || !valid_config(cfg)) return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, keys, vals, offsets, target, ranges, image, t_final, n_contrib, workspace};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (n > 0) {
+        const void* per[] = {means, log_scales, quats, sh, splats, rect, tiles_touched, d_means, d_log_scales,
+                             d_quats, d_opacity_logits, d_sh};
+        for (const void* p : per)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    const Frame f = make_frame(cam, cfg);
+    char* ws_base = static_cast<char*>(workspace);
+    return cuda_status(ws::launch_train(n, means, log_scales, quats, sh, f, num_keys, keys, vals, splats, rect,
+                                        offsets, tiles_touched, target, ranges, image, t_final, n_contrib, d_means,
+                                        d_log_scales, d_quats, d_opacity_logits, d_sh, key_capacity,
+                                        ws_base + layout(0, key_capacity).bwd, static_cast<cudaStream_t>(stream)));
+}
+
+ws_status ws_render_train_l2_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
+                                   const float* sh, int32_t views, const ws_camera* cams, const ws_config* cfg,
+                                   const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals,
+                                   const float* splats, const uint16_t* rect, const uint32_t* offsets,
+                                   const uint32_t* tiles_touched, const float* target, int64_t key_capacity,
+                                   uint32_t* ranges, float* image, float* t_final, uint32_t* n_contrib,
+                                   float* d_means, float* d_log_scales, float* d_quats, float* d_opacity_logits,
+                                   float* d_sh, void* workspace, void* stream) {
+    ws::FrameTable ft;
+    if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 31) || !make_table(views, cams, cfg, ft) ||
+        n * views >= (int64_t(1) << 32))
+        return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, keys, vals, offsets, target, ranges, image, t_final, n_contrib, workspace};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (n > 0) {
+        const void* per[] = {means, log_scales, quats, sh, splats, rect, tiles_touched, d_means, d_log_scales,
+                             d_quats, d_opacity_logits, d_sh};
+        for (const void* p : per)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    char* ws_base = static_cast<char*>(workspace);
+    return cuda_status(ws::launch_train_batch(n, means, log_scales, quats, sh, ft, num_keys, keys, vals, splats, rect,
+                                              offsets, tiles_touched, target, ranges, image, t_final, n_contrib,
+                                              d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, key_capacity,
+                                              (cfg->flags & WS_CFG_PERSISTENT) != 0u,
+                                              ws_base + layout(0, key_capacity).bwd,
+                                              static_cast<cudaStream_t>(stream)));
+}
+
 ws_status ws_image_residual(int64_t count, const float* image, const float* target, float* d_image, void* stream) {
     if (count < 0) return WS_ERR_INVALID_ARG;
     if (count == 0) return WS_OK;

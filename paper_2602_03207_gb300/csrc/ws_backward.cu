@@ -45,6 +45,21 @@ k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                        [offsets](uint32_t g) { return __ldg(offsets + g); }, t_final, n_contrib, d_image, partials);
 }
 
+// One training step's blend of a tile (forward, L2 residual, backward
+// records) in one block: train_tile.
+template <int TS>
+__global__ void __launch_bounds__(TileGeom<TS>::THREADS)
+k_train(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, const float4* __restrict__ splats,
+        const uint2* __restrict__ rect, const uint32_t* __restrict__ offsets, const Frame f,
+        const float* __restrict__ target, float* __restrict__ image, float* __restrict__ t_final,
+        uint32_t* __restrict__ n_contrib, float* __restrict__ partials) {
+    __shared__ BwdSmem<TS> sm;
+    pdl_wait();
+    train_tile<TS>(f, blockIdx.x, ranges[blockIdx.x], vals, splats, rect,
+                   [offsets](uint32_t g) { return __ldg(offsets + g); }, target, image, t_final, n_contrib, partials,
+                   sm);
+}
+
 constexpr int kPbThreads = 128;
 
 __global__ void __launch_bounds__(kPbThreads, 8)
@@ -190,6 +205,49 @@ cudaError_t launch_backward(int64_t n, const float* means, const float* log_scal
             case 32:
                 e = launch_pdl(k_blend_bwd<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, s4, rc, offsets, f,
                                t_final, n_contrib, d_image, partials);
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (n > 0) {
+        const int64_t blocks = (n + kPbThreads - 1) / kPbThreads;
+        e = launch_pdl(k_preprocess_bwd, dim3((unsigned)blocks), dim3(kPbThreads), 0, stream, n, means, log_scales,
+                       reinterpret_cast<const float4*>(quats), reinterpret_cast<const float4*>(sh), f, s4,
+                       offsets, tiles_touched, (uint32_t)key_capacity, (const float*)partials, d_means, d_log_scales,
+                       reinterpret_cast<float4*>(d_quats), d_logits, reinterpret_cast<float4*>(d_sh));
+    }
+    return e;
+}
+
+cudaError_t launch_train(int64_t n, const float* means, const float* log_scales, const float* quats, const float* sh,
+                         const Frame& f, const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals,
+                         const float* splats, const uint16_t* rect, const uint32_t* offsets,
+                         const uint32_t* tiles_touched, const float* target, uint32_t* ranges, float* image,
+                         float* t_final, uint32_t* n_contrib, float* d_means, float* d_log_scales, float* d_quats,
+                         float* d_logits, float* d_sh, int64_t key_capacity, void* scratch, cudaStream_t stream) {
+    float* partials = static_cast<float*>(scratch);
+    const int ntiles = f.TX * f.TY;
+    const float4* s4 = reinterpret_cast<const float4*>(splats);
+    const uint2* rc = reinterpret_cast<const uint2*>(rect);
+    cudaError_t e = cudaSuccess;
+    if (ntiles > 0) {
+        e = launch_tile_ranges(keys, num_keys, ranges, (uint32_t)ntiles, stream);
+        if (e != cudaSuccess) return e;
+        const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
+        switch (f.TS) {
+            case 8:
+                e = launch_pdl(k_train<8>, dim3(ntiles), dim3(TileGeom<8>::THREADS), 0, stream, r2, vals, s4, rc,
+                               offsets, f, target, image, t_final, n_contrib, partials);
+                break;
+            case 16:
+                e = launch_pdl(k_train<16>, dim3(ntiles), dim3(TileGeom<16>::THREADS), 0, stream, r2, vals, s4, rc,
+                               offsets, f, target, image, t_final, n_contrib, partials);
+                break;
+            case 32:
+                e = launch_pdl(k_train<32>, dim3(ntiles), dim3(TileGeom<32>::THREADS), 0, stream, r2, vals, s4, rc,
+                               offsets, f, target, image, t_final, n_contrib, partials);
                 break;
             default:
                 return cudaErrorInvalidValue;

@@ -121,6 +121,33 @@ k_blend_bwd_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__
                        n_contrib + po, d_image + 3 * po, partials);
 }
 
+// One training step's blend over every (view, tile) item: train_tile per
+// item. PERSISTENT = false: one block per item. PERSISTENT = true: a grid of
+// as many blocks as fit on the GPU at once, block b taking items b, b + G,
+// b + 2G, ... (G = the grid size) in that fixed order, so the assignment is
+// static and neighbouring blocks work on neighbouring tiles; no block waits
+// on another.
+template <int TS, bool PERSISTENT>
+__global__ void __launch_bounds__(TileGeom<TS>::THREADS)
+k_train_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, int64_t n,
+              const float4* __restrict__ splats, const uint2* __restrict__ rect,
+              const uint32_t* __restrict__ offsets, const FrameTable ft, const float* __restrict__ target,
+              float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib,
+              float* __restrict__ partials) {
+    __shared__ BwdSmem<TS> sm;
+    pdl_wait();
+    const uint32_t ntiles = ft.tile_off[ft.views];
+    const uint32_t stride = PERSISTENT ? gridDim.x : ntiles;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += stride) {
+        const int v = view_of_tile(ft.tile_off, ft.views, t);
+        const uint64_t vo = (uint64_t)v * (uint64_t)n, po = ft.pix_off[v];
+        const uint32_t* voff = offsets + vo;
+        train_tile<TS>(ft.f[v], (int)(t - ft.tile_off[v]), ranges[t], vals, splats + kSplatVec4 * vo, rect + vo,
+                       [voff](uint32_t g) { return __ldg(voff + g); }, target + 3 * po, image + 3 * po,
+                       t_final + po, n_contrib + po, partials, sm);
+    }
+}
+
 __global__ void __launch_bounds__(kBatchThreads)
 k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* __restrict__ log_scales,
                        const float4* __restrict__ quats, const float4* __restrict__ sh, const FrameTable ft,
@@ -323,6 +350,72 @@ cudaError_t launch_residual(int64_t count, const float* image, const float* targ
     return launch_pdl(k_residual, dim3(sms * 4), dim3(256), 0, stream, count,
                       reinterpret_cast<const float4*>(image), reinterpret_cast<const float4*>(target),
                       reinterpret_cast<float4*>(d_image), count / 4);
+}
+
+template <int TS>
+cudaError_t launch_train_batch_ts(const uint2* r2, const uint32_t* vals, int64_t n, const float4* s4, const uint2* rc,
+                                  const uint32_t* offsets, const FrameTable& ft, const float* target, float* image,
+                                  float* t_final, uint32_t* n_contrib, float* partials, bool persistent,
+                                  cudaStream_t stream) {
+    const uint32_t ntiles = ft.tile_off[ft.views];
+    constexpr int kThreads = TileGeom<TS>::THREADS;
+    if (!persistent)
+        return launch_pdl(k_train_batch<TS, false>, dim3(ntiles), dim3(kThreads), 0, stream, r2, vals, n, s4, rc,
+                          offsets, ft, target, image, t_final, n_contrib, partials);
+    int dev = 0, sms = 148, occ = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_train_batch<TS, true>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    const uint32_t grid = min(ntiles, (uint32_t)(sms * (occ > 0 ? occ : 1)));
+    return launch_pdl(k_train_batch<TS, true>, dim3(grid), dim3(kThreads), 0, stream, r2, vals, n, s4, rc, offsets,
+                      ft, target, image, t_final, n_contrib, partials);
+}
+
+cudaError_t launch_train_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
+                               const float* sh, const FrameTable& ft, const uint32_t* num_keys, const uint64_t* keys,
+                               const uint32_t* vals, const float* splats, const uint16_t* rect,
+                               const uint32_t* offsets, const uint32_t* tiles_touched, const float* target,
+                               uint32_t* ranges, float* image, float* t_final, uint32_t* n_contrib, float* d_means,
+                               float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
+                               int64_t key_capacity, bool persistent, void* scratch, cudaStream_t stream) {
+    float* partials = static_cast<float*>(scratch);
+    const uint32_t ntiles = ft.tile_off[ft.views];
+    const float4* s4 = reinterpret_cast<const float4*>(splats);
+    const uint2* rc = reinterpret_cast<const uint2*>(rect);
+    cudaError_t e = cudaSuccess;
+    if (ntiles > 0) {
+        e = launch_tile_ranges(keys, num_keys, ranges, ntiles, stream);
+        if (e != cudaSuccess) return e;
+        const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
+        switch (ft.f[0].TS) {
+            case 8:
+                e = launch_train_batch_ts<8>(r2, vals, n, s4, rc, offsets, ft, target, image, t_final, n_contrib,
+                                             partials, persistent, stream);
+                break;
+            case 16:
+                e = launch_train_batch_ts<16>(r2, vals, n, s4, rc, offsets, ft, target, image, t_final, n_contrib,
+                                              partials, persistent, stream);
+                break;
+            case 32:
+                e = launch_train_batch_ts<32>(r2, vals, n, s4, rc, offsets, ft, target, image, t_final, n_contrib,
+                                              partials, persistent, stream);
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (n > 0) {
+        const int64_t blocks = (n + kBatchThreads - 1) / kBatchThreads;
+        e = launch_pdl(k_preprocess_bwd_batch, dim3((unsigned)blocks), dim3(kBatchThreads), 0, stream, n, means,
+                       log_scales, reinterpret_cast<const float4*>(quats), reinterpret_cast<const float4*>(sh), ft, s4,
+                       offsets, tiles_touched, (uint32_t)key_capacity, (const float*)partials, d_means,
+                       d_log_scales, reinterpret_cast<float4*>(d_quats), d_logits, reinterpret_cast<float4*>(d_sh));
+    }
+    return e;
 }
 
 }  // namespace ws

@@ -1,5 +1,6 @@
-// Per-tile blend body (paper §3.4 with §2.1's compositing), shared by the
-// single-view and the batched rasterisation kernels.
+// Per-tile blend bodies (paper §3.4 with §2.1's compositing) shared by the
+// single-view, batched and fused training kernels: the forward composite,
+// its deterministic adjoint, and both in one pass over a tile.
 #pragma once
 
 #include <type_traits>
@@ -8,29 +9,20 @@
 
 namespace ws {
 
-constexpr int kBlendBatch = 256;
+constexpr int kBlendBatch = 256;  // splats staged in shared memory at a time
+constexpr int kBwdChunk = 64;     // splats whose partials the backward holds at a time
+constexpr int kPart = 9;          // dmean x, y; dconic a, b, c; sigma dsigma; drgb r, g, b
 
-// Bitmask of the tile's BW x BH pixel blocks (BPR per row, BROWS rows) that
-// a splat at tile-relative (x, y) can reach with alpha >= 1/255 (§3.4), i.e.
-// whose pixel centres meet the bounding box of the ellipse
-// q = a dx^2 + 2 b dx dy + c dy^2 <= qc: half-widths sqrt(qc Sigma'_xx),
-// sqrt(qc Sigma'_yy) with Sigma' = [[c, -b], [-b, a]] / det. The box carries
-// a margin (relative and absolute) well above the error of the approximate
-// reciprocal and square roots, so no pixel that the blend's own test keeps is
-// left out; a block visited without need adds w = 0.
-template <int BW, int BH, int BPR, int BROWS>
-__device__ __forceinline__ uint32_t splat_block_mask(float x, float y, float a, float b, float c, float qc) {
-    const float rdet = rcp_approx(fmaf(a, c, -b * b));
-    const float ex = sqrt_approx(qc * c * rdet) * 1.0001f + 1e-3f;
-    const float ey = sqrt_approx(qc * a * rdet) * 1.0001f + 1e-3f;
-    return box_block_mask<BW, BH, BPR, BROWS>(x - ex, x + ex, y - ey, y + ey);
-}
-
-// Shared-memory record of one splat for the blend (48 bytes).
+// Shared-memory record of one staged splat (48 bytes):
+//   geo  = tile-relative centre x, y; conic premultiplied A = -log2(e) a / 2,
+//          B = -log2(e) b
+//   geo2 = C = -log2(e) c / 2, L = log2(sigma); raw conic a, b
+//   col  = r, g, b; raw conic c
+// The forward reads geo, geo2.xy and col.xyz; the backward everything.
 struct SplatRec {
-    float4 geo;   // tile-relative centre x, y; conic premultiplied A, B
-    float4 geo2;  // C, log2(opacity), -, -
-    float4 col;   // r, g, b, -
+    float4 geo;
+    float4 geo2;
+    float4 col;
 };
 
 // Per-splat inputs of the blend, read from the splat records of
@@ -53,8 +45,32 @@ struct FloatSplats {
     }
 };
 
-// Bitmask of a tile's 4x4 pixel sub-blocks (SPR per row and per column, bit
-// row * SPR + col) whose pixel centres meet the box [xl, xh] x [yl, yh].
+// Geometry of a TS x TS tile: THREADS threads, one per pixel of one 8x4
+// region per warp (PPT regions per warp when the tile has more pixels than
+// threads); each region is two 4x4 sub-blocks, one per half-warp. A splat's
+// mask has one bit per sub-block (row-major, SPR per row).
+template <int TS>
+struct TileGeom {
+    static constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int PPT = TS * TS / THREADS;
+    static constexpr int RPR = TS / 8;  // regions per row
+    static constexpr int SPR = TS / 4;  // sub-blocks per row
+    using Mask = typename std::conditional<(SPR * SPR > 32), unsigned long long, uint32_t>::type;
+    // region k of this warp: lane's pixel (tile-relative, centre) and the
+    // index of the region's left sub-block
+    __device__ static __forceinline__ void pixel(int warp, int lane, int k, float& px, float& py, int& sb) {
+        const int rg = warp + k * WARPS;
+        const int rx = rg % RPR, ry = rg / RPR;
+        px = (float)(rx * 8 + (lane >> 4) * 4 + (lane & 3)) + 0.5f;
+        py = (float)(ry * 4 + ((lane >> 2) & 3)) + 0.5f;
+        sb = ry * SPR + 2 * rx;
+    }
+};
+
+// Bitmask of a tile's 4x4 sub-blocks whose pixel centres meet the box
+// [xl, xh] x [yl, yh] (tile-relative): one compare pair per sub-block column
+// and per sub-block row.
 template <int SPR, typename MaskT>
 __device__ __forceinline__ MaskT box_subblock_mask(float xl, float xh, float yl, float yh) {
     MaskT cols = 0;
@@ -68,90 +84,69 @@ __device__ __forceinline__ MaskT box_subblock_mask(float xl, float xh, float yl,
     return mask;
 }
 
-template <int SPR, typename MaskT>
-__device__ __forceinline__ MaskT splat_subblock_mask(float x, float y, float a, float b, float c, float qc) {
+// Builds the staged record of one splat and the mask of the sub-blocks that
+// the bounding box of its opacity-aware ellipse (§3.4) reaches:
+// q = a dx^2 + 2 b dx dy + c dy^2 <= qc, half-widths sqrt(qc Sigma'_xx),
+// sqrt(qc Sigma'_yy) with Sigma' = [[c, -b], [-b, a]] / det. The box carries a
+// margin (relative and absolute) well above the error of the approximate
+// reciprocal and square roots, so no pixel that the blend's own test keeps is
+// left out; a sub-block visited without need adds w = 0.
+template <int TS, typename Splats>
+__device__ __forceinline__ void stage_splat(const Frame& f, float ox, float oy, const Splats& sp, uint32_t g,
+                                            SplatRec& r, typename TileGeom<TS>::Mask& mask) {
+    float a, b, c, op;
+    sp.load(g, ox, oy, r.geo.x, r.geo.y, a, b, c, op, r.col);
+    r.geo.z = -0.5f * kLog2e * a;
+    r.geo.w = -kLog2e * b;
+    const float L = lg2_approx(op);
+    r.geo2 = make_float4(-0.5f * kLog2e * c, L, a, b);
+    r.col.w = c;
+    const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, kTwoLn2 * (L - kLog2AlphaMin));
     const float rdet = rcp_approx(fmaf(a, c, -b * b));
     const float ex = sqrt_approx(qc * c * rdet) * 1.0001f + 1e-3f;
     const float ey = sqrt_approx(qc * a * rdet) * 1.0001f + 1e-3f;
-    return box_subblock_mask<SPR, MaskT>(x - ex, x + ex, y - ey, y + ey);
+    mask = box_subblock_mask<TileGeom<TS>::SPR, typename TileGeom<TS>::Mask>(r.geo.x - ex, r.geo.x + ex,
+                                                                             r.geo.y - ey, r.geo.y + ey);
 }
 
+// Forward state of a thread's pixels: front to back, C += c a T, T -= a T.
 template <int TS>
-struct SubMask {
-    using T = typename std::conditional<((TS / 4) * (TS / 4) > 32), unsigned long long, uint32_t>::type;
-};
+struct FwdPixels {
+    using G = TileGeom<TS>;
+    float px[G::PPT], py[G::PPT], T[G::PPT], C0[G::PPT], C1[G::PPT], C2[G::PPT];
+    uint32_t last[G::PPT];
+    int sb[G::PPT];
 
-// One block per tile. Each warp owns WPB (TS^2/256, at least 1) 8x4 pixel
-// regions, each split into two 4x4 sub-blocks, one per half-warp. Splats are
-// staged 256 at a time; while staging, every splat also records the bitmask
-// of the tile's 4x4 sub-blocks that the bounding box of its opacity-aware
-// ellipse meets. Each half-warp then walks the batch 32 splats at a time and
-// visits only the splats of its own sub-block, in list order; the two halves
-// run in lockstep for max(visits of either half) steps, the idle half adding
-// w = 0, so per pixel the compositing order and arithmetic are unchanged.
-template <int TS, typename Splats>
-__device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
-                                           const Splats& sp, float* __restrict__ image, float* __restrict__ t_final,
-                                           uint32_t* __restrict__ n_contrib) {
-    constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
-    constexpr int WARPS = THREADS / 32;
-    constexpr int PPT = TS * TS / THREADS;  // 8x4 regions per warp (TS = 32: 4)
-    constexpr int RPR = TS / 8;             // regions per row
-    constexpr int SPR = TS / 4;             // sub-blocks per row
-    using MaskT = typename SubMask<TS>::T;
-    __shared__ SplatRec s_rec[kBlendBatch];
-    __shared__ MaskT s_mask[kBlendBatch];
-
-    const int tx = tile % f.TX, ty = tile / f.TX;
-    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int half = lane >> 4;
-
-    float px[PPT], py[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
-    uint32_t last[PPT];
-    int sba[PPT];
+    __device__ __forceinline__ void init(int warp, int lane) {
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int rg = warp + k * WARPS;
-        const int rx = rg % RPR, ry = rg / RPR;
-        px[k] = (float)(rx * 8 + half * 4 + (lane & 3)) + 0.5f;
-        py[k] = (float)(ry * 4 + ((lane >> 2) & 3)) + 0.5f;
-        sba[k] = ry * SPR + 2 * rx;
-        T[k] = 1.f;
-        C0[k] = C1[k] = C2[k] = 0.f;
-        last[k] = 0;
+        for (int k = 0; k < G::PPT; ++k) {
+            G::pixel(warp, lane, k, px[k], py[k], sb[k]);
+            T[k] = 1.f;
+            C0[k] = C1[k] = C2[k] = 0.f;
+            last[k] = 0;
+        }
     }
 
-    for (uint32_t start = range.x; start < range.y; start += kBlendBatch) {
-        const int cnt = (int)min((uint32_t)kBlendBatch, range.y - start);
-        __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += THREADS) {
-            const uint32_t g = __ldg(vals + start + j);
-            float a, b, c, op;
-            SplatRec r;
-            sp.load(g, ox, oy, r.geo.x, r.geo.y, a, b, c, op, r.col);
-            r.geo.z = -0.5f * kLog2e * a;
-            r.geo.w = -kLog2e * b;
-            const float L = lg2_approx(op);
-            r.geo2 = make_float4(-0.5f * kLog2e * c, L, 0.f, 0.f);
-            s_rec[j] = r;
-            const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, kTwoLn2 * (L - kLog2AlphaMin));
-            s_mask[j] = splat_subblock_mask<SPR, MaskT>(r.geo.x, r.geo.y, a, b, c, qc);
-        }
-        __syncthreads();
-        const uint32_t rel = start + 1 - range.x;
+    // Composites the staged splats [0, cnt) (list positions rel0 - 1 + j, made
+    // 1-based for n_contrib). Each half-warp walks the batch 32 splats at a
+    // time and visits only the splats whose mask has its own sub-block, in
+    // list order; the two halves run in lockstep for max(visits of either
+    // half) steps, the idle half adding w = 0, which leaves C and T bit for
+    // bit unchanged, so per pixel the compositing order and arithmetic are
+    // those of a plain front-to-back loop.
+    __device__ __forceinline__ void batch(const SplatRec* s_rec, const typename G::Mask* s_mask, int cnt,
+                                          uint32_t rel0, int lane) {
+        const int half = lane >> 4;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
+        for (int k = 0; k < G::PPT; ++k) {
             for (int base = 0; base < cnt; base += 32) {
                 const int jj = base + lane;
-                const MaskT m = jj < cnt ? s_mask[jj] : MaskT(0);
-                const uint32_t ba = __ballot_sync(kFull, (uint32_t)(m >> sba[k]) & 1u);
-                const uint32_t bb = __ballot_sync(kFull, (uint32_t)(m >> (sba[k] + 1)) & 1u);
+                const typename G::Mask m = jj < cnt ? s_mask[jj] : typename G::Mask(0);
+                const uint32_t ba = __ballot_sync(kFull, (uint32_t)(m >> sb[k]) & 1u);
+                const uint32_t bb = __ballot_sync(kFull, (uint32_t)(m >> (sb[k] + 1)) & 1u);
                 uint32_t bits = half ? bb : ba;
                 const int steps = max(__popc(ba), __popc(bb));
                 for (int it = 0; it < steps; ++it) {
-                    // The idle half (no splat left) re-reads entry `base` and
-                    // adds w = 0, which leaves C and T bit for bit unchanged.
                     const bool act = bits != 0u;
                     const int j = base + (act ? __ffs(bits) - 1 : 0);
                     bits &= bits - 1u;
@@ -167,231 +162,380 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
                     C1[k] = fmaf(col.y, w, C1[k]);
                     C2[k] = fmaf(col.z, w, C2[k]);
                     T[k] = T[k] - w;
-                    last[k] = keep ? rel + j : last[k];
+                    last[k] = keep ? rel0 + j : last[k];
                 }
             }
         }
     }
-
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int gx = tx * TS + (int)px[k], gy = ty * TS + (int)py[k];
-        if (gx < f.W && gy < f.H) {
-            const size_t pix = (size_t)gy * f.W + gx;
-            image[3 * pix] = fmaf(T[k], f.bg[0], C0[k]);
-            image[3 * pix + 1] = fmaf(T[k], f.bg[1], C1[k]);
-            image[3 * pix + 2] = fmaf(T[k], f.bg[2], C2[k]);
-            t_final[pix] = T[k];
-            n_contrib[pix] = last[k];
-        }
-    }
-}
-
-
-constexpr int kBwdBatch = 64;
-constexpr int kPart = 9;  // dmean x, y; dconic a, b, c; sigma dsigma; drgb r, g, b
-
-struct BwdRec {
-    float4 geo;   // tile-relative centre x, y; premultiplied conic A, B
-    float4 geo2;  // premultiplied C, log2(opacity), conic a, conic b
-    float4 col;   // r, g, b, conic c
 };
 
-// `tile` is the tile index within the frame; `slot_of(g)` gives the first
-// emission slot of Gaussian g's pairs for this frame (offsets[g] for one view,
-// offsets[g * views + v] in a batch).
-template <int TS, typename SlotBase>
-__device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
-                                               const float4* __restrict__ splats, const uint2* __restrict__ rect,
-                                               SlotBase slot_of,
-                                               const float* __restrict__ t_final,
-                                               const uint32_t* __restrict__ n_contrib,
-                                               const float* __restrict__ d_image, float* __restrict__ partials) {
-    constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
-    constexpr int WARPS = THREADS / 32;
-    constexpr int PPT = TS * TS / THREADS;
-    constexpr int BW = 8, BH = 4;
-    constexpr int BPR = TS / BW;
-    constexpr int BROWS = TS / BH;
-    __shared__ BwdRec s_rec[kBwdBatch];
-    __shared__ uint32_t s_mask[kBwdBatch];
-    __shared__ uint32_t s_slot[kBwdBatch];
-    __shared__ float s_part[kBwdBatch][WARPS][kPart];
-    __shared__ uint32_t s_max[WARPS];
+// Backward state of a thread's pixels, walked back to front from the final
+// transmittance. With B = colour behind the splat normalised by the
+// transmittance after it (B starts as the background, B <- a c + (1 - a) B):
+//   dL/dc = a T dL/dC,   dL/da = T (c - B) . dL/dC,
+// and, unless the alpha was clamped at 0.99, sigma dL/dsigma = raw dL/da
+// (raw = sigma G, the unclamped alpha) and dL/dpower = a dL/da with
+// power = -1/2 d^T Q d, giving d/dmean = Q d, d/dQ_a = -dx^2/2,
+// d/dQ_b = -dx dy, d/dQ_c = -dy^2/2.
+template <int TS>
+struct BwdPixels {
+    using G = TileGeom<TS>;
+    float px[G::PPT], py[G::PPT], T[G::PPT], dC[G::PPT][3], Bc[G::PPT][3];
+    uint32_t last[G::PPT];
+    int sb[G::PPT];
+    typename G::Mask wmask;  // sub-blocks of this warp's regions
 
-    const int tx = tile % f.TX, ty = tile / f.TX;
-    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t len = range.y - range.x;
-
-    float px[PPT], py[PPT], T[PPT], dC[PPT][3], Bc[PPT][3];
-    uint32_t last[PPT];
-    uint32_t wmask = 0;  // union of this warp's block bits
-    uint32_t my_max = 0;
+    __device__ __forceinline__ void init_geometry(int warp, int lane) {
+        wmask = 0;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int b = warp + k * WARPS;
-        wmask |= 1u << b;
-        const int bx = (b % BPR) * BW, by = (b / BPR) * BH;
-        const int lx = bx + (lane & 7), ly = by + (lane >> 3);
-        px[k] = (float)lx + 0.5f;
-        py[k] = (float)ly + 0.5f;
-        const int gx = tx * TS + lx, gy = ty * TS + ly;
-        const bool inside = gx < f.W && gy < f.H;
-        const size_t pix = inside ? (size_t)gy * f.W + gx : 0;
-        T[k] = inside ? t_final[pix] : 1.f;
-        last[k] = inside ? n_contrib[pix] : 0u;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            dC[k][c] = inside ? d_image[3 * pix + c] : 0.f;
-            Bc[k][c] = f.bg[c];
+        for (int k = 0; k < G::PPT; ++k) {
+            G::pixel(warp, lane, k, px[k], py[k], sb[k]);
+            wmask |= typename G::Mask(3) << sb[k];
         }
-        my_max = max(my_max, last[k]);
     }
-    // Block-wide maximum of the last-contributor counts: positions past it
-    // are never composited, their records are zero.
-    for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(kFull, my_max, o));
-    if (lane == 0) s_max[warp] = my_max;
-    __syncthreads();
-    uint32_t max_last = 0;
-#pragma unroll
-    for (int w = 0; w < WARPS; ++w) max_last = max(max_last, s_max[w]);
 
-    // Zero records for list positions no pixel composited.
-    for (uint32_t j = max_last + threadIdx.x; j < len; j += THREADS) {
-        const uint32_t g = __ldg(vals + range.x + j);
-        const uint2 r = __ldg(rect + g);
-        const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
-        const uint32_t slot = slot_of(g) + (ty - y0) * (x1 - x0 + 1) + (tx - x0);
+    // Walks the staged splats [0, cnt) back to front (list positions pos0 +
+    // j), in chunks of kBwdChunk: every warp that has a composited pixel for
+    // a splat sums the splat's 9 partials over its 32 pixels in a fixed order
+    // and stores them in s_part[j][warp]; the block then adds the warps in
+    // warp order and writes one record per pair at its emission slot.
+    __device__ __forceinline__ void batch(const SplatRec* s_rec, const typename G::Mask* s_mask,
+                                          const uint32_t* s_slot, float (*s_part)[G::WARPS][kPart],
+                                          uint32_t* s_wrote, int cnt, uint32_t pos0, int warp, int lane,
+                                          float* __restrict__ partials) {
+        for (int hi = cnt; hi > 0; hi -= kBwdChunk) {
+            const int lo = max(0, hi - kBwdChunk);
+            for (int j = threadIdx.x; j < hi - lo; j += G::THREADS) s_wrote[j] = 0u;
+            __syncthreads();
+            for (int base = lo + (((hi - lo - 1) >> 5) << 5); base >= lo; base -= 32) {
+                const int jj = base + lane;
+                uint32_t bits = __ballot_sync(kFull, jj < hi && (s_mask[jj] & wmask) != 0u);
+                while (bits) {
+                    const int hb = 31 - __clz(bits);
+                    bits &= ~(1u << hb);
+                    const int j = base + hb;
+                    const uint32_t pos = pos0 + (uint32_t)j;
+                    const SplatRec r = s_rec[j];
+                    const typename G::Mask m = s_mask[j];
+                    float acc[kPart];
+#pragma unroll
+                    for (int c = 0; c < kPart; ++c) acc[c] = 0.f;
+                    bool any = false;
+#pragma unroll
+                    for (int k = 0; k < G::PPT; ++k) {
+                        if (!((uint32_t)(m >> sb[k]) & 3u)) continue;  // warp-uniform
+                        if (pos >= last[k]) continue;
+                        const float dx = px[k] - r.geo.x, dy = py[k] - r.geo.y;
+                        const float e = splat_log2_alpha(dx, dy, r.geo.z, r.geo.w, r.geo2.x, r.geo2.y);
+                        if (!(e >= kLog2AlphaMin)) continue;
+                        const float raw = ex2_approx(e);
+                        const float alpha = fminf(kAlphaMax, raw);
+                        any = true;
+                        // T before this pair, T_after / (1 - alpha), with the
+                        // reciprocal on the special-function unit (a few ulp;
+                        // 1 - alpha >= 0.01)
+                        const float Tb = T[k] * rcp_approx(1.f - alpha);
+                        const float w = alpha * Tb;
+                        float dalpha = 0.f;
+                        const float cc[3] = {r.col.x, r.col.y, r.col.z};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            acc[6 + c] = fmaf(w, dC[k][c], acc[6 + c]);
+                            dalpha = fmaf(cc[c] - Bc[k][c], dC[k][c], dalpha);
+                            Bc[k][c] = fmaf(alpha, cc[c] - Bc[k][c], Bc[k][c]);
+                        }
+                        dalpha *= Tb;
+                        T[k] = Tb;
+                        if (raw < kAlphaMax) {
+                            // partial 5 is sigma dL/dsigma = raw dL/dalpha
+                            // (d alpha / d sigma = exp(-q/2) = raw / sigma)
+                            acc[5] = fmaf(raw, dalpha, acc[5]);
+                            const float dp = alpha * dalpha;
+                            const float ca = r.geo2.z, cb = r.geo2.w, cc2 = r.col.w;
+                            acc[0] = fmaf(dp, ca * dx + cb * dy, acc[0]);
+                            acc[1] = fmaf(dp, cb * dx + cc2 * dy, acc[1]);
+                            acc[2] = fmaf(dp, -0.5f * dx * dx, acc[2]);
+                            acc[3] = fmaf(dp, -dx * dy, acc[3]);
+                            acc[4] = fmaf(dp, -0.5f * dy * dy, acc[4]);
+                        }
+                    }
+                    if (__any_sync(kFull, any)) {
+                        // Warp sums of the 9 partials in a fixed order with 14
+                        // shuffles: partials 0..7 by reduce-scatter (each step
+                        // hands half of a lane's values to its partner, so after
+                        // offsets 16, 8, 4 lane l holds partial (l >> 2) & 7
+                        // summed over 8 lanes, then two butterfly steps finish
+                        // it), partial 8 by a butterfly.
+                        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+                        float h4[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float give = b4 ? acc[q] : acc[4 + q];
+                            const float keep = b4 ? acc[4 + q] : acc[q];
+                            h4[q] = keep + __shfl_xor_sync(kFull, give, 16);
+                        }
+                        float h2[2];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const float give = b3 ? h4[q] : h4[2 + q];
+                            const float keep = b3 ? h4[2 + q] : h4[q];
+                            h2[q] = keep + __shfl_xor_sync(kFull, give, 8);
+                        }
+                        float h1 = (b2 ? h2[1] : h2[0]) + __shfl_xor_sync(kFull, b2 ? h2[0] : h2[1], 4);
+                        h1 += __shfl_xor_sync(kFull, h1, 2);
+                        h1 += __shfl_xor_sync(kFull, h1, 1);
+                        float v8 = acc[8];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(kFull, v8, o);
+                        if ((lane & 3) == 0) s_part[j - lo][warp][lane >> 2] = h1;
+                        if (lane == 0) {
+                            s_part[j - lo][warp][8] = v8;
+                            atomicOr(s_wrote + (j - lo), 1u << warp);  // which warps hold a partial
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // Block sum over the warps that wrote, in warp order, one record per pair.
+            for (int e = threadIdx.x; e < (hi - lo) * kPart; e += G::THREADS) {
+                const int j = e / kPart, c = e - j * kPart;
+                const uint32_t wr = s_wrote[j];
+                float s = 0.f;
+#pragma unroll
+                for (int w = 0; w < G::WARPS; ++w) s += ((wr >> w) & 1u) ? s_part[j][w][c] : 0.f;
+                partials[(size_t)s_slot[lo + j] * kPart + c] = s;
+            }
+            __syncthreads();
+        }
+    }
+};
+
+// Emission slot of the pair (tile (tx, ty), Gaussian g): its first slot
+// slot_of(g) plus the tile's row-major rank in g's rectangle.
+template <typename SlotBase>
+__device__ __forceinline__ uint32_t pair_slot(SlotBase slot_of, const uint2* __restrict__ rect, uint32_t g, int tx,
+                                              int ty) {
+    const uint2 rc = __ldg(rect + g);
+    const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+    return slot_of(g) + (ty - y0) * (x1 - x0 + 1) + (tx - x0);
+}
+
+// Block-wide maximum of the last-contributor counts (positions past it are
+// never composited; their records are zero).
+template <int TS>
+__device__ __forceinline__ uint32_t block_max_last(const uint32_t* last, uint32_t* s_max, int warp, int lane) {
+    using G = TileGeom<TS>;
+    uint32_t my = 0;
+#pragma unroll
+    for (int k = 0; k < G::PPT; ++k) my = max(my, last[k]);
+    for (int o = 16; o > 0; o >>= 1) my = max(my, __shfl_xor_sync(kFull, my, o));
+    if (lane == 0) s_max[warp] = my;
+    __syncthreads();
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < G::WARPS; ++w) m = max(m, s_max[w]);
+    return m;
+}
+
+// Zero records for list positions [from, len) that no pixel composited.
+template <typename SlotBase>
+__device__ __forceinline__ void zero_records(uint2 range, uint32_t from, const uint32_t* __restrict__ vals,
+                                             const uint2* __restrict__ rect, SlotBase slot_of, int tx, int ty,
+                                             int threads, float* __restrict__ partials) {
+    const uint32_t len = range.y - range.x;
+    for (uint32_t j = from + threadIdx.x; j < len; j += threads) {
+        const uint32_t slot = pair_slot(slot_of, rect, __ldg(vals + range.x + j), tx, ty);
         float* dst = partials + (size_t)slot * kPart;
 #pragma unroll
         for (int c = 0; c < kPart; ++c) dst[c] = 0.f;
     }
+}
 
-    for (int end = (int)max_last; end > 0; end -= kBwdBatch) {
-        const int lo = max(0, end - kBwdBatch);
-        const int cnt = end - lo;
+// Stages list positions [start, start + cnt) of a tile: records and masks,
+// and (WITH_SLOT) each pair's emission slot.
+template <int TS, bool WITH_SLOT, typename Splats, typename SlotBase>
+__device__ __forceinline__ void stage_batch(const Frame& f, float ox, float oy, int tx, int ty, uint32_t start,
+                                            int cnt, const uint32_t* __restrict__ vals, const Splats& sp,
+                                            const uint2* __restrict__ rect, SlotBase slot_of, SplatRec* s_rec,
+                                            typename TileGeom<TS>::Mask* s_mask, uint32_t* s_slot) {
+    for (int j = threadIdx.x; j < cnt; j += TileGeom<TS>::THREADS) {
+        const uint32_t g = __ldg(vals + start + j);
+        SplatRec r;
+        typename TileGeom<TS>::Mask m;
+        stage_splat<TS>(f, ox, oy, sp, g, r, m);
+        s_rec[j] = r;
+        s_mask[j] = m;
+        if (WITH_SLOT) s_slot[j] = pair_slot(slot_of, rect, g, tx, ty);
+    }
+}
+
+struct NoSlot {
+    __device__ __forceinline__ uint32_t operator()(uint32_t) const { return 0u; }
+};
+
+// Forward of one tile: stages the list 256 splats at a time and composites
+// each batch (FwdPixels::batch), then writes image = C + T bg, the final
+// transmittance and the 1-based list position of the last composited splat.
+template <int TS, typename Splats>
+__device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
+                                           const Splats& sp, float* __restrict__ image, float* __restrict__ t_final,
+                                           uint32_t* __restrict__ n_contrib) {
+    using G = TileGeom<TS>;
+    __shared__ SplatRec s_rec[kBlendBatch];
+    __shared__ typename G::Mask s_mask[kBlendBatch];
+    const int tx = tile % f.TX, ty = tile / f.TX;
+    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    FwdPixels<TS> P;
+    P.init(warp, lane);
+    for (uint32_t start = range.x; start < range.y; start += kBlendBatch) {
+        const int cnt = (int)min((uint32_t)kBlendBatch, range.y - start);
         __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += THREADS) {
-            const uint32_t g = __ldg(vals + range.x + lo + j);
-            const float4 m = __ldg(splats + kSplatVec4 * g);
-            const float4 k = __ldg(splats + kSplatVec4 * g + 1);
-            const float4 cl = __ldg(splats + kSplatVec4 * g + 2);
-            const float a = k.x, b = k.y, c = k.z, op = k.w;
-            BwdRec r;
-            r.geo.x = __fadd_rn(__fsub_rn(m.x, ox), m.z);
-            r.geo.y = __fadd_rn(__fsub_rn(m.y, oy), m.w);
-            r.geo.z = -0.5f * kLog2e * a;
-            r.geo.w = -kLog2e * b;
-            const float L = lg2_approx(op);
-            r.geo2 = make_float4(-0.5f * kLog2e * c, L, a, b);
-            r.col = make_float4(cl.x, cl.y, cl.z, c);
-            s_rec[j] = r;
-            const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, kTwoLn2 * (L - kLog2AlphaMin));
-            s_mask[j] = splat_block_mask<BW, BH, BPR, BROWS>(r.geo.x, r.geo.y, a, b, c, qc);
-            const uint2 rc = __ldg(rect + g);
-            const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
-            s_slot[j] = slot_of(g) + (ty - y0) * (x1 - x0 + 1) + (tx - x0);
+        stage_batch<TS, false>(f, ox, oy, tx, ty, start, cnt, vals, sp, nullptr, NoSlot{}, s_rec, s_mask, nullptr);
+        __syncthreads();
+        P.batch(s_rec, s_mask, cnt, start + 1 - range.x, lane);
+    }
+#pragma unroll
+    for (int k = 0; k < G::PPT; ++k) {
+        const int gx = tx * TS + (int)P.px[k], gy = ty * TS + (int)P.py[k];
+        if (gx < f.W && gy < f.H) {
+            const size_t pix = (size_t)gy * f.W + gx;
+            image[3 * pix] = fmaf(P.T[k], f.bg[0], P.C0[k]);
+            image[3 * pix + 1] = fmaf(P.T[k], f.bg[1], P.C1[k]);
+            image[3 * pix + 2] = fmaf(P.T[k], f.bg[2], P.C2[k]);
+            t_final[pix] = P.T[k];
+            n_contrib[pix] = P.last[k];
         }
-        for (int e = threadIdx.x; e < cnt * WARPS * kPart; e += THREADS) (&s_part[0][0][0])[e] = 0.f;
-        __syncthreads();
+    }
+}
 
-        // Back to front over the batch: chunks of 32 from the top, highest
-        // set bit first.
-        for (int base = ((cnt - 1) >> 5) << 5; base >= 0; base -= 32) {
-            const int jj = base + lane;
-            uint32_t bits = __ballot_sync(kFull, jj < cnt && (s_mask[jj] & wmask) != 0u);
-            while (bits) {
-                const int hb = 31 - __clz(bits);
-                bits &= ~(1u << hb);
-                const int j = base + hb;
-                const uint32_t pos = (uint32_t)(lo + j);
-                const BwdRec r = s_rec[j];
-                const uint32_t m = s_mask[j];
-                float acc[kPart];
+// Shared memory of the backward and fused kernels, staging BATCH splats.
+template <int TS, int BATCH = kBlendBatch>
+struct BwdSmem {
+    SplatRec rec[BATCH];
+    typename TileGeom<TS>::Mask mask[BATCH];
+    uint32_t slot[BATCH];
+    float part[kBwdChunk][TileGeom<TS>::WARPS][kPart];
+    uint32_t wrote[kBwdChunk];
+    uint32_t maxl[TileGeom<TS>::WARPS];
+};
+
+// Backward of one tile from the stored forward outputs: each pair's 9
+// partials at its emission slot (see BwdPixels), staging kBwdChunk splats at
+// a time (the smaller shared-memory footprint keeps more blocks resident).
+// `slot_of(g)` gives the first emission slot of Gaussian g's pairs for this
+// frame (offsets[g] for one view, offsets[v * n + g] in a batch).
+template <int TS, typename SlotBase>
+__device__ __forceinline__ void blend_bwd_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
+                                               const float4* __restrict__ splats, const uint2* __restrict__ rect,
+                                               SlotBase slot_of, const float* __restrict__ t_final,
+                                               const uint32_t* __restrict__ n_contrib,
+                                               const float* __restrict__ d_image, float* __restrict__ partials) {
+    using G = TileGeom<TS>;
+    __shared__ BwdSmem<TS, kBwdChunk> sm;
+    const int tx = tile % f.TX, ty = tile / f.TX;
+    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const FloatSplats sp{splats};
+    BwdPixels<TS> B;
+    B.init_geometry(warp, lane);
 #pragma unroll
-                for (int c = 0; c < kPart; ++c) acc[c] = 0.f;
-                bool any = false;
+    for (int k = 0; k < G::PPT; ++k) {
+        const int gx = tx * TS + (int)B.px[k], gy = ty * TS + (int)B.py[k];
+        const bool inside = gx < f.W && gy < f.H;
+        const size_t pix = inside ? (size_t)gy * f.W + gx : 0;
+        B.T[k] = inside ? t_final[pix] : 1.f;
+        B.last[k] = inside ? n_contrib[pix] : 0u;
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (!((m >> (warp + k * WARPS)) & 1u)) continue;  // warp-uniform
-                    if (pos >= last[k]) continue;
-                    const float dx = px[k] - r.geo.x, dy = py[k] - r.geo.y;
-                    const float e = splat_log2_alpha(dx, dy, r.geo.z, r.geo.w, r.geo2.x, r.geo2.y);
-                    if (!(e >= kLog2AlphaMin)) continue;
-                    const float raw = ex2_approx(e);
-                    const float alpha = fminf(kAlphaMax, raw);
-                    any = true;
-                    // T before this pair, T_after / (1 - alpha), with the
-                    // reciprocal on the special-function unit (a few ulp;
-                    // 1 - alpha >= 0.01)
-                    const float Tb = T[k] * rcp_approx(1.f - alpha);
-                    const float w = alpha * Tb;
-                    float dalpha = 0.f;
-                    const float cc[3] = {r.col.x, r.col.y, r.col.z};
+        for (int c = 0; c < 3; ++c) {
+            B.dC[k][c] = inside ? d_image[3 * pix + c] : 0.f;
+            B.Bc[k][c] = f.bg[c];
+        }
+    }
+    const uint32_t max_last = block_max_last<TS>(B.last, sm.maxl, warp, lane);
+    zero_records(range, max_last, vals, rect, slot_of, tx, ty, G::THREADS, partials);
+    // batches of the composited prefix [0, max_last), last batch first
+    const int nb = (int)((max_last + kBwdChunk - 1) / kBwdChunk);
+    for (int b = nb - 1; b >= 0; --b) {
+        const uint32_t lo = (uint32_t)b * kBwdChunk;
+        const int cnt = (int)min((uint32_t)kBwdChunk, max_last - lo);
+        __syncthreads();
+        stage_batch<TS, true>(f, ox, oy, tx, ty, range.x + lo, cnt, vals, sp, rect, slot_of, sm.rec, sm.mask,
+                              sm.slot);
+        __syncthreads();
+        B.batch(sm.rec, sm.mask, sm.slot, sm.part, sm.wrote, cnt, lo, warp, lane, partials);
+    }
+}
+
+// One training step's blend of one tile in a single pass: the forward
+// composite (bit-identical to blend_tile), image and final transmittance
+// written, the L2 residual d = image - target formed in registers, then the
+// backward of BwdPixels over the same list. When the tile's list fits one
+// batch (most tiles), the backward reuses the forward's staged records.
+template <int TS, typename SlotBase>
+__device__ __forceinline__ void train_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
+                                           const float4* __restrict__ splats, const uint2* __restrict__ rect,
+                                           SlotBase slot_of, const float* __restrict__ target,
+                                           float* __restrict__ image, float* __restrict__ t_final,
+                                           uint32_t* __restrict__ n_contrib, float* __restrict__ partials,
+                                           BwdSmem<TS>& sm) {
+    using G = TileGeom<TS>;
+    const int tx = tile % f.TX, ty = tile / f.TX;
+    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const FloatSplats sp{splats};
+    const uint32_t len = range.y - range.x;
+    const int nb = (int)((len + kBlendBatch - 1) / kBlendBatch);
+    BwdPixels<TS> B;
+    {
+        FwdPixels<TS> P;
+        P.init(warp, lane);
+        for (int b = 0; b < nb; ++b) {
+            const uint32_t lo = (uint32_t)b * kBlendBatch;
+            const int cnt = (int)min((uint32_t)kBlendBatch, len - lo);
+            __syncthreads();
+            stage_batch<TS, true>(f, ox, oy, tx, ty, range.x + lo, cnt, vals, sp, rect, slot_of, sm.rec, sm.mask,
+                                  sm.slot);
+            __syncthreads();
+            P.batch(sm.rec, sm.mask, cnt, lo + 1, lane);
+        }
+        B.init_geometry(warp, lane);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        acc[6 + c] = fmaf(w, dC[k][c], acc[6 + c]);
-                        dalpha = fmaf(cc[c] - Bc[k][c], dC[k][c], dalpha);
-                        Bc[k][c] = fmaf(alpha, cc[c] - Bc[k][c], Bc[k][c]);
-                    }
-                    dalpha *= Tb;
-                    T[k] = Tb;
-                    if (raw < kAlphaMax) {
-                        // partial 5 is sigma dL/dsigma = raw dL/dalpha
-                        // (d alpha / d sigma = exp(-q/2) = raw / sigma)
-                        acc[5] = fmaf(raw, dalpha, acc[5]);
-                        const float dp = alpha * dalpha;
-                        const float ca = r.geo2.z, cb = r.geo2.w, cc2 = r.col.w;
-                        acc[0] = fmaf(dp, ca * dx + cb * dy, acc[0]);
-                        acc[1] = fmaf(dp, cb * dx + cc2 * dy, acc[1]);
-                        acc[2] = fmaf(dp, -0.5f * dx * dx, acc[2]);
-                        acc[3] = fmaf(dp, -dx * dy, acc[3]);
-                        acc[4] = fmaf(dp, -0.5f * dy * dy, acc[4]);
-                    }
-                }
-                if (__any_sync(kFull, any)) {
-                    // Warp sums of the 9 partials in a fixed order with 14
-                    // shuffles: partials 0..7 by reduce-scatter (each step
-                    // hands half of a lane's values to its partner, so after
-                    // offsets 16, 8, 4 lane l holds partial (l >> 2) & 7
-                    // summed over 8 lanes, then two butterfly steps finish
-                    // it), partial 8 by a butterfly.
-                    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-                    float h4[4];
+        for (int k = 0; k < G::PPT; ++k) {
+            const int gx = tx * TS + (int)P.px[k], gy = ty * TS + (int)P.py[k];
+            const bool inside = gx < f.W && gy < f.H;
+            const size_t pix = inside ? (size_t)gy * f.W + gx : 0;
+            const float img[3] = {fmaf(P.T[k], f.bg[0], P.C0[k]), fmaf(P.T[k], f.bg[1], P.C1[k]),
+                                  fmaf(P.T[k], f.bg[2], P.C2[k])};
+            if (inside) {
+                image[3 * pix] = img[0];
+                image[3 * pix + 1] = img[1];
+                image[3 * pix + 2] = img[2];
+                t_final[pix] = P.T[k];
+                n_contrib[pix] = P.last[k];
+            }
+            B.T[k] = inside ? P.T[k] : 1.f;
+            B.last[k] = inside ? P.last[k] : 0u;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float give = b4 ? acc[q] : acc[4 + q];
-                        const float keep = b4 ? acc[4 + q] : acc[q];
-                        h4[q] = keep + __shfl_xor_sync(kFull, give, 16);
-                    }
-                    float h2[2];
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const float give = b3 ? h4[q] : h4[2 + q];
-                        const float keep = b3 ? h4[2 + q] : h4[q];
-                        h2[q] = keep + __shfl_xor_sync(kFull, give, 8);
-                    }
-                    float h1 = (b2 ? h2[1] : h2[0]) + __shfl_xor_sync(kFull, b2 ? h2[0] : h2[1], 4);
-                    h1 += __shfl_xor_sync(kFull, h1, 2);
-                    h1 += __shfl_xor_sync(kFull, h1, 1);
-                    float v8 = acc[8];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(kFull, v8, o);
-                    if ((lane & 3) == 0) s_part[j][warp][lane >> 2] = h1;
-                    if (lane == 0) s_part[j][warp][8] = v8;
-                }
+            for (int c = 0; c < 3; ++c) {
+                B.dC[k][c] = inside ? img[c] - __ldg(target + 3 * pix + c) : 0.f;
+                B.Bc[k][c] = f.bg[c];
             }
         }
-        __syncthreads();
-        // Block sum over warps in warp order, one record per pair.
-        for (int e = threadIdx.x; e < cnt * kPart; e += THREADS) {
-            const int j = e / kPart, c = e - j * kPart;
-            float s = 0.f;
-#pragma unroll
-            for (int w = 0; w < WARPS; ++w) s += s_part[j][w][c];
-            partials[(size_t)s_slot[j] * kPart + c] = s;
+    }
+    const uint32_t max_last = block_max_last<TS>(B.last, sm.maxl, warp, lane);
+    zero_records(range, max_last, vals, rect, slot_of, tx, ty, G::THREADS, partials);
+    const int nbb = (int)((max_last + kBlendBatch - 1) / kBlendBatch);
+    for (int b = nbb - 1; b >= 0; --b) {
+        const uint32_t lo = (uint32_t)b * kBlendBatch;
+        const int cnt = (int)min((uint32_t)kBlendBatch, max_last - lo);
+        if (b != nb - 1) {  // the last forward batch is still staged
+            __syncthreads();
+            stage_batch<TS, true>(f, ox, oy, tx, ty, range.x + lo, cnt, vals, sp, rect, slot_of, sm.rec, sm.mask,
+                                  sm.slot);
         }
+        __syncthreads();
+        B.batch(sm.rec, sm.mask, sm.slot, sm.part, sm.wrote, cnt, lo, warp, lane, partials);
     }
 }
 

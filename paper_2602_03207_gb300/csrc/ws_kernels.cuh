@@ -110,4 +110,20 @@ cudaError_t launch_backward_batch(int64_t n, const float* means, const float* lo
 cudaError_t launch_residual(int64_t count, const float* image, const float* target, float* d_image,
                             cudaStream_t stream);
 
+// ---- fused training step (blend forward + L2 residual + backward records,
+// then the per-Gaussian adjoint)
+cudaError_t launch_train(int64_t n, const float* means, const float* log_scales, const float* quats, const float* sh,
+                         const Frame& f, const uint32_t* num_keys, const uint64_t* keys, const uint32_t* vals,
+                         const float* splats, const uint16_t* rect, const uint32_t* offsets,
+                         const uint32_t* tiles_touched, const float* target, uint32_t* ranges, float* image,
+                         float* t_final, uint32_t* n_contrib, float* d_means, float* d_log_scales, float* d_quats,
+                         float* d_logits, float* d_sh, int64_t key_capacity, void* scratch, cudaStream_t stream);
+cudaError_t launch_train_batch(int64_t n, const float* means, const float* log_scales, const float* quats,
+                               const float* sh, const FrameTable& ft, const uint32_t* num_keys, const uint64_t* keys,
+                               const uint32_t* vals, const float* splats, const uint16_t* rect,
+                               const uint32_t* offsets, const uint32_t* tiles_touched, const float* target,
+                               uint32_t* ranges, float* image, float* t_final, uint32_t* n_contrib, float* d_means,
+                               float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
+                               int64_t key_capacity, bool persistent, void* scratch, cudaStream_t stream);
+
 }  // namespace ws

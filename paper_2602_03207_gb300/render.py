@@ -207,6 +207,36 @@ class Renderer:
                                    g["opacity_logits"], g["sh"], self.workspace, stream)
         return {k: v[:self.n] for k, v in g.items()}
 
+    def train_step_l2(self, scene, cam_dict, target, stream=None):
+        """One training step of L = 1/2 ||image - target||^2 in fused form
+        (ws_render_train_l2 after the pre-processing, compaction and sort):
+        the same image and gradients as forward() + ws_image_residual +
+        backward(), in fewer launches. Returns the gradient dict."""
+        if self.packed:
+            raise ValueError("the packed-record variant renders only (no backward)")
+        cam = capi.camera(cam_dict)
+        self.preprocess(scene, cam, stream)
+        self.cull(cam, stream)
+        self.sort(stream)
+        g = self._grads()
+        capi.ws_render_train_l2(self.n, scene["means"], scene["log_scales"], scene["quats"], scene["sh"], cam,
+                                self.cfg, self.num_keys, self.sorted_keys, self.sorted_vals, self.splats, self.rect,
+                                self.offsets, self.tiles_touched, target.contiguous(), self.key_capacity,
+                                self.ranges, self.image, self.t_final, self.n_contrib, g["means"], g["log_scales"],
+                                g["quats"], g["opacity_logits"], g["sh"], self.workspace, stream)
+        return {k: v[:self.n] for k, v in g.items()}
+
+    def _grads(self):
+        if getattr(self, "grads", None) is None:
+            d = self.image.device
+            n1 = max(self.n, 1)
+            self.grads = {"means": torch.empty((n1, 3), dtype=torch.float32, device=d),
+                          "log_scales": torch.empty((n1, 3), dtype=torch.float32, device=d),
+                          "quats": torch.empty((n1, 4), dtype=torch.float32, device=d),
+                          "opacity_logits": torch.empty(n1, dtype=torch.float32, device=d),
+                          "sh": torch.empty((n1, 16, 3), dtype=torch.float32, device=d)}
+        return self.grads
+
     def check_status(self, stream=None):
         """Synchronises and raises if the frame overflowed its key capacity."""
         flags = capi.ws_read_status(self.workspace, clear=False, stream=stream)

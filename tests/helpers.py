@@ -96,3 +96,38 @@ def compare_image(g, ref, tile_mask=None, atol=IMAGE_ATOL):
         stats["examples"] = [(tuple(i), float(e0[tuple(i)]), float(e1[tuple(i)]), int(ref["n_amb"][tuple(i)]))
                              for i in idx]
     return stats
+
+
+# ---- workers for the full-size batched test (spawned processes; no GPU)
+
+def c5_target(cam, v):
+    """Seeded U[0,1) target image of view v of the batched workload."""
+    return np.random.default_rng(1000 + v).random((cam["height"], cam["width"], 3)).astype(np.float32)
+
+
+def oracle_tiles_of_view(job):
+    """FP64 oracle image of view `v` of the 2,000,000-Gaussian batch scene
+    on the listed 16x16 tiles, returned as per-tile crops."""
+    import oracle
+    from paper_2602_03207_gb300 import synthetic as S
+    v, tiles = job
+    scene, cam = S.batch_scene(), S.batch_views()[v]
+    ref = oracle.render(scene, cam, tile_list=np.asarray(tiles))
+    tx = (cam["width"] + 15) // 16
+    out = []
+    for t in tiles:
+        y0, x0 = (t // tx) * 16, (t % tx) * 16
+        sl = (slice(y0, y0 + 16), slice(x0, x0 + 16))
+        out.append({k: ref[k][sl] for k in ("image", "alt_image", "t_final", "alt_t_final", "n_amb")})
+    return v, out
+
+
+def oracle_grad_of_view(job):
+    """FP64 oracle gradient of view `v` for every `stride`-th Gaussian of the
+    batch scene against the view's seeded target."""
+    import oracle
+    from paper_2602_03207_gb300 import synthetic as S
+    v, stride = job
+    scene = {k: np.ascontiguousarray(a[::stride]) for k, a in S.batch_scene().items()}
+    cam = S.batch_views()[v]
+    return oracle.loss_grad(scene, cam, c5_target(cam, v))["grads"]

@@ -137,3 +137,38 @@ def test_autograd_step_captures_in_a_cuda_graph():
     for k in NAMES:
         got = params[k].grad.cpu().numpy().astype(np.float64)
         assert rel(got, ref[k].reshape(got.shape)) <= 1e-3, k
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_fused_train_step_equals_separate_calls(tile):
+    """ws_render_train_l2 (forward, L2 residual and backward records in one
+    pass per tile) gives the image, final transmittance, last-contributor
+    counts and gradients of ws_rasterize + ws_image_residual +
+    ws_rasterize_backward bit for bit, and the gradients match the oracle."""
+    import torch
+    from paper_2602_03207_gb300 import capi, render
+    scene, cam = S.small_forward()
+    sub = {k: v[:3000] for k, v in scene.items()}
+    target = np.random.default_rng(13).random((256, 256, 3)).astype(np.float32)
+    tgt = torch.as_tensor(target, device="cuda")
+    dev = render.scene_to_device(sub)
+    r = render.Renderer(3000, 256, 256, tile=tile, key_capacity=16 * 3000)
+    img = r.forward(dev, cam)
+    d = torch.empty_like(tgt)
+    capi.ws_image_residual(tgt.numel(), img, tgt, d)
+    ga = r.backward(dev, cam, d)
+    torch.cuda.synchronize()
+    a = {"image": img.cpu().numpy(), "t_final": r.t_final.cpu().numpy(), "n_contrib": r.n_contrib.cpu().numpy(),
+         **{k: v.cpu().numpy() for k, v in ga.items()}}
+    r2 = render.Renderer(3000, 256, 256, tile=tile, key_capacity=16 * 3000)
+    gb = r2.train_step_l2(dev, cam, tgt)
+    r2.check_status()
+    torch.cuda.synchronize()
+    b = {"image": r2.image.cpu().numpy(), "t_final": r2.t_final.cpu().numpy(),
+         "n_contrib": r2.n_contrib.cpu().numpy(), **{k: v.cpu().numpy() for k, v in gb.items()}}
+    for k in a:
+        np.testing.assert_array_equal(b[k], a[k], err_msg=k)
+    ref = oracle.loss_grad(sub, cam, target, tile=tile)["grads"]
+    for k in NAMES:
+        got = b[k].astype(np.float64)
+        assert rel(got, ref[k].reshape(got.shape)) <= 1e-3, k
