@@ -865,6 +865,21 @@ def batch_block(args, dev, min_timed_s=1.0, plain_min_s=0.5):
     t_batch = t_region / steps
     pairs = b.key_count()
     del g
+    # the fused single-pass step, on one block per (view, tile) and on the
+    # persistent grid (same results bit for bit; timed the same way)
+    variants = {}
+    for name, fused, persistent in (("fused_grid", True, False), ("fused_persistent", True, True)):
+        bv = batch.BatchRenderer(n, cams, tile=best["tile"], digit_bits=best["digit_bits"],
+                                 key_capacity=best["key_capacity"], device=dev, fused=fused, persistent=persistent)
+        gv = bv.capture(scene, tgt)
+        for _ in range(3):
+            gv.replay()
+        torch.cuda.synchronize()
+        _, tv, _ = timed_regions(lambda o, k: [gv.replay() for _ in range(k)], steps, stream, 0.3, max_regions=5)
+        bv.check_status()
+        variants[name] = {"ms_per_step": round(tv / steps * 1e3, 3), "views_s": round(V / (tv / steps), 2)}
+        del gv, bv
+        torch.cuda.empty_cache()
     # per-stage split of the batched step (eager launches, an event between stages)
     names = ("preprocess", "cull", "sort", "rasterize", "residual", "backward")
     reps = 5
@@ -912,6 +927,9 @@ def batch_block(args, dev, min_timed_s=1.0, plain_min_s=0.5):
                    "autotune": best.get("table"), "autotune_cached": best.get("cached")},
         "stages_ms": {k: round(v, 3) for k, v in stage_ms.items()},
         "stages_note": "eager launches with an event between stages; the timed step is one CUDA-graph replay",
+        "step_variants": variants,
+        "step_variants_note": "the timed step runs the separate forward / residual / backward calls; the fused "
+                              "single pass per (view, tile) and its persistent grid give the same results",
         "roofline": {"kernel": f"k_blend_bwd_batch<{best['tile']}> (timed span: ws_rasterize_backward_batch)",
                      "bound": "alu", "alg_evals": int(evals), "achieved": round(ach, 3), "peak": round(peak, 2),
                      "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,

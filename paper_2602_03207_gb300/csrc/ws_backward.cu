@@ -17,8 +17,9 @@
 //   giving d/dmean = Q d, d/dQ_a = -dx^2/2, d/dQ_b = -dx dy, d/dQ_c = -dy^2/2.
 //   (The sigma partial is kept multiplied by sigma: dL/dlogit is then that
 //   sum times 1 - sigma.)
-//   Each warp reduces its 32 pixels with a fixed shuffle tree, the block
-//   adds its warps in warp order, and the record goes to the pair's slot.
+//   Each half-warp (a 4x4 pixel sub-block) reduces its 16 pixels with a
+//   fixed shuffle tree, the block adds its half-warps in order, and the
+//   record goes to the pair's slot.
 // k_preprocess_bwd: one thread per Gaussian: slot-ordered sum of its
 //   records, then the adjoint of conic = Sigma'^{-1}, Sigma' = T Sigma T^T,
 //   T = J W (J's guard-band clamp passes no gradient), the projection of

@@ -195,114 +195,126 @@ struct BwdPixels {
     }
 
     // Walks the staged splats [0, cnt) back to front (list positions pos0 +
-    // j), in chunks of kBwdChunk: every warp that has a composited pixel for
-    // a splat sums the splat's 9 partials over its 32 pixels in a fixed order
-    // and stores them in s_part[j][warp]; the block then adds the warps in
-    // warp order and writes one record per pair at its emission slot.
+    // j), in chunks of kBwdChunk. Each half-warp visits, back to front, the
+    // splats whose mask has its own 4x4 sub-block; the two halves run in
+    // lockstep for max(visits of either half) steps (an idle half evaluates
+    // nothing). Each half sums its splat's 9 partials over its 16 pixels in
+    // a fixed order and stores them in s_part[j][half-warp]; the block then
+    // adds the half-warps that wrote, in order, and writes one record per
+    // pair at its emission slot.
     __device__ __forceinline__ void batch(const SplatRec* s_rec, const typename G::Mask* s_mask,
-                                          const uint32_t* s_slot, float (*s_part)[G::WARPS][kPart],
+                                          const uint32_t* s_slot, float (*s_part)[2 * G::WARPS][kPart],
                                           uint32_t* s_wrote, int cnt, uint32_t pos0, int warp, int lane,
                                           float* __restrict__ partials) {
+        const int half = lane >> 4;
+        const int hw = 2 * warp + half;  // this lane's half-warp
         for (int hi = cnt; hi > 0; hi -= kBwdChunk) {
             const int lo = max(0, hi - kBwdChunk);
             for (int j = threadIdx.x; j < hi - lo; j += G::THREADS) s_wrote[j] = 0u;
             __syncthreads();
-            for (int base = lo + (((hi - lo - 1) >> 5) << 5); base >= lo; base -= 32) {
-                const int jj = base + lane;
-                uint32_t bits = __ballot_sync(kFull, jj < hi && (s_mask[jj] & wmask) != 0u);
-                while (bits) {
-                    const int hb = 31 - __clz(bits);
-                    bits &= ~(1u << hb);
-                    const int j = base + hb;
-                    const uint32_t pos = pos0 + (uint32_t)j;
-                    const SplatRec r = s_rec[j];
-                    const typename G::Mask m = s_mask[j];
-                    float acc[kPart];
 #pragma unroll
-                    for (int c = 0; c < kPart; ++c) acc[c] = 0.f;
-                    bool any = false;
+            for (int k = 0; k < G::PPT; ++k) {
+                for (int base = lo + (((hi - lo - 1) >> 5) << 5); base >= lo; base -= 32) {
+                    const int jj = base + lane;
+                    const typename G::Mask mm = jj < hi ? s_mask[jj] : typename G::Mask(0);
+                    const uint32_t ba = __ballot_sync(kFull, (uint32_t)(mm >> sb[k]) & 1u);
+                    const uint32_t bb = __ballot_sync(kFull, (uint32_t)(mm >> (sb[k] + 1)) & 1u);
+                    uint32_t bits = half ? bb : ba;
+                    const int steps = max(__popc(ba), __popc(bb));
+                    for (int it = 0; it < steps; ++it) {
+                        const bool act = bits != 0u;
+                        const int hb = act ? 31 - __clz(bits) : 0;
+                        bits &= ~(1u << hb);
+                        const int j = base + hb;
+                        const uint32_t pos = pos0 + (uint32_t)j;
+                        float acc[kPart];
 #pragma unroll
-                    for (int k = 0; k < G::PPT; ++k) {
-                        if (!((uint32_t)(m >> sb[k]) & 3u)) continue;  // warp-uniform
-                        if (pos >= last[k]) continue;
-                        const float dx = px[k] - r.geo.x, dy = py[k] - r.geo.y;
-                        const float e = splat_log2_alpha(dx, dy, r.geo.z, r.geo.w, r.geo2.x, r.geo2.y);
-                        if (!(e >= kLog2AlphaMin)) continue;
-                        const float raw = ex2_approx(e);
-                        const float alpha = fminf(kAlphaMax, raw);
-                        any = true;
-                        // T before this pair, T_after / (1 - alpha), with the
-                        // reciprocal on the special-function unit (a few ulp;
-                        // 1 - alpha >= 0.01)
-                        const float Tb = T[k] * rcp_approx(1.f - alpha);
-                        const float w = alpha * Tb;
-                        float dalpha = 0.f;
-                        const float cc[3] = {r.col.x, r.col.y, r.col.z};
+                        for (int c = 0; c < kPart; ++c) acc[c] = 0.f;
+                        bool any = false;
+                        if (act && pos < last[k]) {
+                            const SplatRec r = s_rec[j];
+                            const float dx = px[k] - r.geo.x, dy = py[k] - r.geo.y;
+                            const float e = splat_log2_alpha(dx, dy, r.geo.z, r.geo.w, r.geo2.x, r.geo2.y);
+                            if (e >= kLog2AlphaMin) {
+                                const float raw = ex2_approx(e);
+                                const float alpha = fminf(kAlphaMax, raw);
+                                any = true;
+                                const float Tb = T[k] * rcp_approx(1.f - alpha);
+                                const float w = alpha * Tb;
+                                float dalpha = 0.f;
+                                const float cc[3] = {r.col.x, r.col.y, r.col.z};
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            acc[6 + c] = fmaf(w, dC[k][c], acc[6 + c]);
-                            dalpha = fmaf(cc[c] - Bc[k][c], dC[k][c], dalpha);
-                            Bc[k][c] = fmaf(alpha, cc[c] - Bc[k][c], Bc[k][c]);
+                                for (int c = 0; c < 3; ++c) {
+                                    acc[6 + c] = w * dC[k][c];
+                                    dalpha = fmaf(cc[c] - Bc[k][c], dC[k][c], dalpha);
+                                    Bc[k][c] = fmaf(alpha, cc[c] - Bc[k][c], Bc[k][c]);
+                                }
+                                dalpha *= Tb;
+                                T[k] = Tb;
+                                if (raw < kAlphaMax) {
+                                    acc[5] = raw * dalpha;
+                                    const float dp = alpha * dalpha;
+                                    const float ca = r.geo2.z, cb = r.geo2.w, cc2 = r.col.w;
+                                    acc[0] = dp * (ca * dx + cb * dy);
+                                    acc[1] = dp * (cb * dx + cc2 * dy);
+                                    acc[2] = dp * (-0.5f * dx * dx);
+                                    acc[3] = dp * (-dx * dy);
+                                    acc[4] = dp * (-0.5f * dy * dy);
+                                }
+                            }
                         }
-                        dalpha *= Tb;
-                        T[k] = Tb;
-                        if (raw < kAlphaMax) {
-                            // partial 5 is sigma dL/dsigma = raw dL/dalpha
-                            // (d alpha / d sigma = exp(-q/2) = raw / sigma)
-                            acc[5] = fmaf(raw, dalpha, acc[5]);
-                            const float dp = alpha * dalpha;
-                            const float ca = r.geo2.z, cb = r.geo2.w, cc2 = r.col.w;
-                            acc[0] = fmaf(dp, ca * dx + cb * dy, acc[0]);
-                            acc[1] = fmaf(dp, cb * dx + cc2 * dy, acc[1]);
-                            acc[2] = fmaf(dp, -0.5f * dx * dx, acc[2]);
-                            acc[3] = fmaf(dp, -dx * dy, acc[3]);
-                            acc[4] = fmaf(dp, -0.5f * dy * dy, acc[4]);
-                        }
-                    }
-                    if (__any_sync(kFull, any)) {
-                        // Warp sums of the 9 partials in a fixed order with 14
-                        // shuffles: partials 0..7 by reduce-scatter (each step
-                        // hands half of a lane's values to its partner, so after
-                        // offsets 16, 8, 4 lane l holds partial (l >> 2) & 7
-                        // summed over 8 lanes, then two butterfly steps finish
-                        // it), partial 8 by a butterfly.
-                        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-                        float h4[4];
+                        const uint32_t anyb = __ballot_sync(kFull, any);
+                        if (anyb) {
+                            // Sums over each half's 16 lanes in a fixed order, 12
+                            // shuffles for both halves: partials 0..7 by
+                            // reduce-scatter (offsets 8, 4, 2; lane l of a half then
+                            // holds partial (l >> 1) & 7 over 8 lanes) and a last
+                            // butterfly step (offset 1), partial 8 by a butterfly.
+                            const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+                            float h4[4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float give = b4 ? acc[q] : acc[4 + q];
-                            const float keep = b4 ? acc[4 + q] : acc[q];
-                            h4[q] = keep + __shfl_xor_sync(kFull, give, 16);
-                        }
-                        float h2[2];
+                            for (int q = 0; q < 4; ++q) {
+                                const float give = b3 ? acc[q] : acc[4 + q];
+                                const float keep = b3 ? acc[4 + q] : acc[q];
+                                h4[q] = keep + __shfl_xor_sync(kFull, give, 8);
+                            }
+                            float h2[2];
 #pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            const float give = b3 ? h4[q] : h4[2 + q];
-                            const float keep = b3 ? h4[2 + q] : h4[q];
-                            h2[q] = keep + __shfl_xor_sync(kFull, give, 8);
-                        }
-                        float h1 = (b2 ? h2[1] : h2[0]) + __shfl_xor_sync(kFull, b2 ? h2[0] : h2[1], 4);
-                        h1 += __shfl_xor_sync(kFull, h1, 2);
-                        h1 += __shfl_xor_sync(kFull, h1, 1);
-                        float v8 = acc[8];
+                            for (int q = 0; q < 2; ++q) {
+                                const float give = b2 ? h4[q] : h4[2 + q];
+                                const float keep = b2 ? h4[2 + q] : h4[q];
+                                h2[q] = keep + __shfl_xor_sync(kFull, give, 4);
+                            }
+                            float h1 = (b1 ? h2[1] : h2[0]) + __shfl_xor_sync(kFull, b1 ? h2[0] : h2[1], 2);
+                            h1 += __shfl_xor_sync(kFull, h1, 1);
+                            float v8 = acc[8];
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(kFull, v8, o);
-                        if ((lane & 3) == 0) s_part[j - lo][warp][lane >> 2] = h1;
-                        if (lane == 0) {
-                            s_part[j - lo][warp][8] = v8;
-                            atomicOr(s_wrote + (j - lo), 1u << warp);  // which warps hold a partial
+                            for (int o = 8; o > 0; o >>= 1) v8 += __shfl_xor_sync(kFull, v8, o);
+                            const bool mine = (anyb >> (16 * half)) & 0xffffu;  // this half has a partial
+                            if (mine) {
+                                // with several regions per warp, a half-warp adds to
+                                // what it stored for the same splat in an earlier region
+                                const bool add = G::PPT > 1 && ((s_wrote[j - lo] >> hw) & 1u);
+                                const int p = ((lane & 15) >> 1);
+                                if ((lane & 1) == 0) s_part[j - lo][hw][p] = add ? s_part[j - lo][hw][p] + h1 : h1;
+                                if ((lane & 15) == 0) {
+                                    s_part[j - lo][hw][8] = add ? s_part[j - lo][hw][8] + v8 : v8;
+                                    atomicOr(s_wrote + (j - lo), 1u << hw);
+                                }
+                            }
                         }
                     }
                 }
+                __syncwarp();  // this region's stores and flags before the next region's reads
             }
             __syncthreads();
-            // Block sum over the warps that wrote, in warp order, one record per pair.
+            // Block sum over the half-warps that wrote, in order, one record per pair.
             for (int e = threadIdx.x; e < (hi - lo) * kPart; e += G::THREADS) {
                 const int j = e / kPart, c = e - j * kPart;
                 const uint32_t wr = s_wrote[j];
                 float s = 0.f;
 #pragma unroll
-                for (int w = 0; w < G::WARPS; ++w) s += ((wr >> w) & 1u) ? s_part[j][w][c] : 0.f;
+                for (int w = 0; w < 2 * G::WARPS; ++w) s += ((wr >> w) & 1u) ? s_part[j][w][c] : 0.f;
                 partials[(size_t)s_slot[lo + j] * kPart + c] = s;
             }
             __syncthreads();
@@ -415,7 +427,7 @@ struct BwdSmem {
     SplatRec rec[BATCH];
     typename TileGeom<TS>::Mask mask[BATCH];
     uint32_t slot[BATCH];
-    float part[kBwdChunk][TileGeom<TS>::WARPS][kPart];
+    float part[kBwdChunk][2 * TileGeom<TS>::WARPS][kPart];
     uint32_t wrote[kBwdChunk];
     uint32_t maxl[TileGeom<TS>::WARPS];
 };

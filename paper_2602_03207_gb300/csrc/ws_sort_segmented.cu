@@ -132,10 +132,16 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&v)[K]) {
     }
 }
 
+// Index of element e in a warp's staging slice: one padding element after
+// every 8, so the transposing accesses (lane l touching element l*K + k)
+// fall in distinct banks: word 9l + k for K = 8.
+__device__ __forceinline__ int spad(int e) { return e + (e >> 3); }
+
 // One warp sorts n <= 32*K pairs [b, b + n) of (kin, vin) into (kout, vout):
-// the pairs are staged in the warp's slice of shared memory, the network
-// sorts (sub-key << 32 | input index) -- unique values, so equal sub-keys
-// keep their input order -- and the pairs are written out in that order.
+// the pairs are staged in the warp's slice of shared memory (keys and sort
+// indices padded, see spad), the network sorts (sub-key << 32 | input index)
+// -- unique values, so equal sub-keys keep their input order -- and the pairs
+// are written out in that order.
 template <int K>
 __device__ void warp_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, uint32_t b,
                           int n, int begin_bit, uint64_t* buf_k, uint32_t* buf_v, uint32_t* buf_i) {
@@ -145,7 +151,7 @@ __device__ void warp_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* ko
     for (int k = 0; k < K; ++k) {
         const int idx = k * kWarp + lane;
         if (idx < n) {
-            buf_k[idx] = __ldg(kin + b + idx);
+            buf_k[spad(idx)] = __ldg(kin + b + idx);
             buf_v[idx] = __ldg(vin + b + idx);
         }
     }
@@ -154,21 +160,21 @@ __device__ void warp_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* ko
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int e = lane * K + k;
-        v[k] = e < n ? ((uint64_t)sub_key(buf_k[e], begin_bit, sub_mask) << 32) | (uint32_t)e : ~0ull;
+        v[k] = e < n ? ((uint64_t)sub_key(buf_k[spad(e)], begin_bit, sub_mask) << 32) | (uint32_t)e : ~0ull;
     }
     warp_bitonic<K>(v);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int e = lane * K + k;
-        if (e < n) buf_i[e] = (uint32_t)v[k];
+        if (e < n) buf_i[spad(e)] = (uint32_t)v[k];
     }
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int p = k * kWarp + lane;
         if (p < n) {
-            const uint32_t src = buf_i[p];
-            kout[b + p] = buf_k[src];
+            const uint32_t src = buf_i[spad(p)];
+            kout[b + p] = buf_k[spad((int)src)];
             vout[b + p] = buf_v[src];
         }
     }
@@ -412,9 +418,17 @@ __device__ void block_sort_global(uint64_t* kin, uint32_t* vin, uint64_t* kout, 
 __global__ void __launch_bounds__(kSegThreads, 4)
 k_seg_sort(uint64_t* kin, uint32_t* vin, uint64_t* kout, uint32_t* vout, const uint32_t* __restrict__ start,
            const uint32_t* __restrict__ num_keys, uint32_t cap, uint32_t nseg, int begin_bit) {
-    __shared__ __align__(16) uint64_t s_key[kCtaCap];
-    __shared__ __align__(16) uint32_t s_val[kCtaCap];
-    __shared__ uint32_t s_cnt[kSegWarps][kLocalRadix];
+    // One buffer, carved two ways: the block paths' key / value / digit
+    // count arrays, or each warp's padded staging slice (keys, values, sort
+    // indices) for the warp path.
+    constexpr int kPadCap = kWarpCap + kWarpCap / 8;
+    constexpr int kWarpBytes = kPadCap * 8 + kWarpCap * 4 + kPadCap * 4;
+    constexpr int kBlockBytes = kCtaCap * 8 + kCtaCap * 4 + kSegWarps * kLocalRadix * 4;
+    constexpr int kRawBytes = kSegWarps * kWarpBytes > kBlockBytes ? kSegWarps * kWarpBytes : kBlockBytes;
+    __shared__ __align__(16) unsigned char s_raw[kRawBytes];
+    uint64_t* s_key = reinterpret_cast<uint64_t*>(s_raw);
+    uint32_t* s_val = reinterpret_cast<uint32_t*>(s_raw + kCtaCap * 8);
+    auto s_cnt = reinterpret_cast<uint32_t (*)[kLocalRadix]>(s_raw + kCtaCap * 12);
     __shared__ uint32_t s_off[kLocalRadix];
     __shared__ uint32_t s_red[2 * kSegWarps + 2];
     const int warp = threadIdx.x >> 5;
@@ -442,9 +456,10 @@ k_seg_sort(uint64_t* kin, uint32_t* vin, uint64_t* kout, uint32_t* vout, const u
     bounds(s, b, e);
     const int n = (int)(e - b);
     if (n == 0 || n > kWarpCap) return;
-    uint64_t* bk = s_key + warp * kWarpCap;
-    uint32_t* bv = s_val + warp * kWarpCap;
-    uint32_t* bi = s_cnt[warp];
+    unsigned char* wraw = s_raw + warp * kWarpBytes;
+    uint64_t* bk = reinterpret_cast<uint64_t*>(wraw);
+    uint32_t* bv = reinterpret_cast<uint32_t*>(wraw + kPadCap * 8);
+    uint32_t* bi = reinterpret_cast<uint32_t*>(wraw + kPadCap * 8 + kWarpCap * 4);
     if (n <= 32)
         warp_sort<1>(kin, vin, kout, vout, b, n, begin_bit, bk, bv, bi);
     else if (n <= 64)
