@@ -102,6 +102,7 @@ typedef struct ws_config {
 #define WS_CFG_FIXED_RADIUS 8u    /* ablation: every splat's box as at sigma = 1 (no opacity-aware extent) */
 #define WS_CFG_SORT_SEGMENTED 16u /* ws_sort: partition by bits [31, end) then sort each segment on chip */
 #define WS_CFG_PERSISTENT 32u     /* ws_render_train_l2_batch: one persistent grid over every (view, tile) */
+#define WS_CFG_RANGES_GIVEN 64u   /* rasterize / train calls: `ranges` already holds the tile ranges (ws_sort_tiles) */
 
 /* Library ABI version (WS_ABI_VERSION of the build). */
 int32_t ws_abi_version(void);
@@ -210,6 +211,22 @@ ws_status ws_sort(const uint32_t *num_keys, int64_t key_capacity, int32_t begin_
  * sort region holds the 2^(end_bit - 31) + 1 segment starts (about one per
  * key of capacity, at most 2^24 + 1); otherwise ws_sort runs the default sort. Segments of more than 2048 keys are sorted by one block
  * through global memory, correct at any size but slower. */
+
+/* The segmented sort of (tile << 31 | depth) keys over bits [0, end_bit)
+ * (ws_sort with WS_CFG_SORT_SEGMENTED and begin_bit 0) that also writes the
+ * tile ranges the rasterisation needs: ranges[t] = [start, end) of tile t in
+ * the sorted list for t < ntiles (start = end for a tile without pairs),
+ * found from the segment boundaries the sort computes anyway. Pass
+ * WS_CFG_RANGES_GIVEN to the following ws_rasterize (or training call) of the
+ * frame so that it takes `ranges` as given instead of scanning the sorted keys
+ * again. ranges (device): ntiles uint32 pairs; ntiles <= 2^(end_bit - 31).
+ * Returns WS_ERR_UNSUPPORTED where ws_sort would fall back to the full-key
+ * passes (end_bit outside 32..55, or a workspace too small for the segment
+ * starts); other errors as ws_sort. */
+ws_status ws_sort_tiles(const uint32_t *num_keys, int64_t key_capacity, int32_t end_bit, uint64_t *keys,
+                        uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, const ws_config *cfg,
+                        void *workspace, uint32_t *ranges, int64_t ntiles, int32_t *result_in_alt,
+                        void *stream);
 
 /* Test hook of the look-back variant: tile `stalled_tile` of the first pass
  * never publishes its counts, so every later tile's bounded wait runs out.

@@ -14,7 +14,7 @@ import math
 import torch
 
 from . import capi
-from .render import SCENE_KEYS, config_flags, tile_grid
+from .render import SCENE_KEYS, config_flags, sort_frame, tile_grid
 
 
 class BatchRenderer:
@@ -104,12 +104,11 @@ class BatchRenderer:
                            self.keys, self.vals, self.key_capacity, self.num_keys, self.workspace, stream)
 
     def sort(self, stream=None):
-        self.sorted_in_alt = capi.ws_sort(self.num_keys, self.key_capacity, 0, self.end_bit, self.keys, self.vals,
-                                          self.keys_alt, self.vals_alt, self.cfg, self.workspace, stream)
+        sort_frame(self, self.total_tiles, stream)
 
     def rasterize(self, stream=None):
         capi.ws_rasterize_batch(self.num_keys, self.sorted_keys, self.sorted_vals, self.n, self.splats,
-                                self.cams_arr, self.cfg, self.ranges, self.image, self.t_final, self.n_contrib,
+                                self.cams_arr, self.raster_cfg, self.ranges, self.image, self.t_final, self.n_contrib,
                                 stream)
 
     def residual(self, target, stream=None):
@@ -150,7 +149,7 @@ class BatchRenderer:
         self.sort(stream)
         g = self.grads
         capi.ws_render_train_l2_batch(self.n, scene["means"], scene["log_scales"], scene["quats"], scene["sh"],
-                                      self.cams_arr, self.cfg, self.num_keys, self.sorted_keys, self.sorted_vals,
+                                      self.cams_arr, self.raster_cfg, self.num_keys, self.sorted_keys, self.sorted_vals,
                                       self.splats, self.rect, self.offsets, self.tiles_touched, target,
                                       self.key_capacity, self.ranges, self.image, self.t_final, self.n_contrib,
                                       g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"],

@@ -25,6 +25,7 @@ WS_FLAG_CAPACITY, WS_FLAG_TIMEOUT = 1, 2
 WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL, WS_CFG_SORT_LOOKBACK, WS_CFG_FIXED_RADIUS = 1, 2, 4, 8
 WS_CFG_SORT_SEGMENTED = 16
 WS_CFG_PERSISTENT = 32
+WS_CFG_RANGES_GIVEN = 64
 WS_ABI_VERSION = 2
 WS_SPLAT_FLOATS = 12  # floats per splat record: centre hi/lo (4), conic (3), sigma, colour (3), 0
 
@@ -32,7 +33,8 @@ EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_prepr
            "ws_sort", "ws_sort_noalloc", "ws_sort_noalloc_max_keys", "ws_rasterize",
            "ws_rasterize_backward", "ws_read_status", "ws_batch_max_views", "ws_batch_workspace_bytes",
            "ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
-           "ws_image_residual", "ws_sort_test_stalled_tile", "ws_render_train_l2", "ws_render_train_l2_batch")
+           "ws_image_residual", "ws_sort_test_stalled_tile", "ws_render_train_l2", "ws_render_train_l2_batch",
+           "ws_sort_tiles")
 
 
 class WsError(RuntimeError):
@@ -100,6 +102,8 @@ def lib():
                                                 P, I64, P, P, P, P, P, P, P]
             L.ws_sort_test_stalled_tile.argtypes = [P, I64, I32, I32, P, P, P, P, cfg_p, P, I32, C.POINTER(I32), P]
             L.ws_sort_test_stalled_tile.restype = I32
+            L.ws_sort_tiles.argtypes = [P, I64, I32, P, P, P, P, cfg_p, P, P, I64, C.POINTER(I32), P]
+            L.ws_sort_tiles.restype = I32
             L.ws_sort_noalloc.argtypes = [P, I64, I32, I32, P, P, P, P, I32, C.POINTER(I32), P]
             L.ws_sort_noalloc.restype = I32
             L.ws_sort_noalloc_max_keys.restype = I64
@@ -175,6 +179,16 @@ def ws_sort(num_keys, key_capacity, begin_bit, end_bit, keys, vals, keys_alt, va
         _ptr(num_keys), int(key_capacity), int(begin_bit), int(end_bit), _ptr(keys), _ptr(vals),
         _ptr(keys_alt), _ptr(vals_alt), C.byref(cfg), _ptr(workspace), C.byref(in_alt),
         _stream(stream)))
+    return bool(in_alt.value)
+
+
+def ws_sort_tiles(num_keys, key_capacity, end_bit, keys, vals, keys_alt, vals_alt, cfg, workspace, ranges, ntiles,
+                  stream=None) -> bool:
+    """Segmented sort that also writes the tile ranges; True when the result is in the _alt buffers."""
+    in_alt = C.c_int32(0)
+    _check("ws_sort_tiles", lib().ws_sort_tiles(
+        _ptr(num_keys), int(key_capacity), int(end_bit), _ptr(keys), _ptr(vals), _ptr(keys_alt), _ptr(vals_alt),
+        C.byref(cfg), _ptr(workspace), _ptr(ranges), int(ntiles), C.byref(in_alt), _stream(stream)))
     return bool(in_alt.value)
 
 

@@ -215,6 +215,33 @@ ws_status ws_sort(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_
     return cuda_status(e);
 }
 
+ws_status ws_sort_tiles(const uint32_t* num_keys, int64_t key_capacity, int32_t end_bit, uint64_t* keys,
+                        uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, const ws_config* cfg,
+                        void* workspace, uint32_t* ranges, int64_t ntiles, int32_t* result_in_alt, void* stream) {
+    if (!cfg || !ws::sort_digit_supported(cfg->digit_bits)) return WS_ERR_UNSUPPORTED;
+    if (key_capacity < 0 || key_capacity >= (int64_t(1) << 31) || end_bit > 64 || end_bit < 1 || !result_in_alt ||
+        ntiles < 0)
+        return WS_ERR_INVALID_ARG;
+    if (!ws::sort_segmented_supported(key_capacity, 0, end_bit)) return WS_ERR_UNSUPPORTED;
+    if (ntiles > (int64_t(1) << (end_bit - 31))) return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {num_keys, workspace, ranges};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (key_capacity > 0) {
+        const void* kp[] = {keys, vals, keys_alt, vals_alt};
+        for (const void* p : kp)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    char* ws_base = static_cast<char*>(workspace);
+    int in_alt = 0;
+    const cudaError_t e = ws::launch_sort_segmented(num_keys, key_capacity, 0, end_bit, cfg->digit_bits, keys, vals,
+                                                    keys_alt, vals_alt, ws_base + layout(0, key_capacity).sort,
+                                                    &in_alt, static_cast<cudaStream_t>(stream), ranges,
+                                                    (uint32_t)ntiles);
+    *result_in_alt = in_alt;
+    return cuda_status(e);
+}
+
 ws_status ws_sort_test_stalled_tile(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_bit,
                                     int32_t end_bit, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
                                     uint32_t* vals_alt, const ws_config* cfg, void* workspace, int32_t stalled_tile,

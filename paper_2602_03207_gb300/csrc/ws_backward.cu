@@ -234,7 +234,7 @@ cudaError_t launch_train(int64_t n, const float* means, const float* log_scales,
     const uint2* rc = reinterpret_cast<const uint2*>(rect);
     cudaError_t e = cudaSuccess;
     if (ntiles > 0) {
-        e = launch_tile_ranges(keys, num_keys, ranges, (uint32_t)ntiles, stream);
+        e = launch_tile_ranges(keys, num_keys, ranges, (uint32_t)ntiles, f.flags, stream);
         if (e != cudaSuccess) return e;
         const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
         switch (f.TS) {

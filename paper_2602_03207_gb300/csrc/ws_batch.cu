@@ -279,7 +279,7 @@ cudaError_t launch_rasterize_batch(const uint32_t* num_keys, const uint64_t* key
                                    uint32_t* n_contrib, cudaStream_t stream) {
     const uint32_t ntiles = ft.tile_off[ft.views];
     if (ntiles == 0) return cudaSuccess;
-    cudaError_t e = launch_tile_ranges(keys, num_keys, ranges, ntiles, stream);
+    cudaError_t e = launch_tile_ranges(keys, num_keys, ranges, ntiles, ft.f[0].flags, stream);
     if (e != cudaSuccess) return e;
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
     const float4* s4 = reinterpret_cast<const float4*>(splats);
@@ -387,7 +387,7 @@ cudaError_t launch_train_batch(int64_t n, const float* means, const float* log_s
     const uint2* rc = reinterpret_cast<const uint2*>(rect);
     cudaError_t e = cudaSuccess;
     if (ntiles > 0) {
-        e = launch_tile_ranges(keys, num_keys, ranges, ntiles, stream);
+        e = launch_tile_ranges(keys, num_keys, ranges, ntiles, ft.f[0].flags, stream);
         if (e != cudaSuccess) return e;
         const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
         switch (ft.f[0].TS) {

@@ -37,9 +37,12 @@ cudaError_t launch_sort(const uint32_t* num_keys, int64_t key_capacity, int begi
 // single-sweep (decoupled look-back) variant
 bool sort_segmented_supported(int64_t key_capacity, int begin_bit, int end_bit);
 size_t sort_segmented_scratch_bytes(int64_t key_capacity);
+// ranges (optional, ntiles entries of [start, end)): each segment's bounds
+// in the sorted output, for the segments below ntiles.
 cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,
                                   int digit_bits, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
-                                  uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream);
+                                  uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream,
+                                  uint32_t* ranges = nullptr, uint32_t ntiles = 0);
 bool sort_lookback_supported(int digit_bits, int begin_bit, int end_bit);
 size_t sort_lookback_scratch_bytes(int64_t key_capacity);
 cudaError_t launch_sort_lookback(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,
@@ -56,8 +59,9 @@ cudaError_t launch_sort_noalloc(const uint32_t* num_keys, int64_t key_capacity, 
                                 cudaStream_t stream);
 
 // ---- rasterisation
+// Skipped (ranges taken as given) when flags has WS_CFG_RANGES_GIVEN.
 cudaError_t launch_tile_ranges(const uint64_t* keys, const uint32_t* num_keys, uint32_t* ranges, uint32_t ntiles,
-                               cudaStream_t stream);
+                               uint32_t flags, cudaStream_t stream);
 cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t key_capacity_hint,
                              const uint64_t* keys, const uint32_t* vals, const float* splats,
                              const Frame& f, uint32_t* ranges, float* image, float* t_final,

@@ -234,7 +234,7 @@ cudaError_t launch_rasterize_packed(const uint32_t* num_keys, const uint64_t* ke
                                     cudaStream_t stream) {
     const int ntiles = f.TX * f.TY;
     if (ntiles == 0) return cudaSuccess;
-    cudaError_t e = launch_tile_ranges(keys, num_keys, ranges, (uint32_t)ntiles, stream);
+    cudaError_t e = launch_tile_ranges(keys, num_keys, ranges, (uint32_t)ntiles, f.flags, stream);
     if (e != cudaSuccess) return e;
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
     const float2* m2 = reinterpret_cast<const float2*>(mean2d);

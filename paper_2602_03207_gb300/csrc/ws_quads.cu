@@ -308,7 +308,7 @@ cudaError_t launch_render_quads(int64_t n, const float* splats, const float* dep
     if (e != cudaSuccess) return e;
     const uint64_t* pk = part_alt ? keys_alt : keys;
     const uint32_t* pv = part_alt ? vals_alt : vals;
-    e = launch_tile_ranges(pk, num_keys, reinterpret_cast<uint32_t*>(ranges), (uint32_t)ntiles, stream);
+    e = launch_tile_ranges(pk, num_keys, reinterpret_cast<uint32_t*>(ranges), (uint32_t)ntiles, 0u, stream);
     if (e != cudaSuccess) return e;
     // 4. back-to-front quads per tile
     switch (f.TS) {

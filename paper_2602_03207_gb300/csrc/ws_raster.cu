@@ -60,7 +60,8 @@ k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, con
 }  // namespace
 
 cudaError_t launch_tile_ranges(const uint64_t* keys, const uint32_t* num_keys, uint32_t* ranges, uint32_t ntiles,
-                               cudaStream_t stream) {
+                               uint32_t flags, cudaStream_t stream) {
+    if (flags & WS_CFG_RANGES_GIVEN) return cudaSuccess;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -74,7 +75,7 @@ cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t /*key_capacity_hi
                              uint32_t* n_contrib, cudaStream_t stream) {
     const int ntiles = f.TX * f.TY;
     if (ntiles == 0) return cudaSuccess;
-    cudaError_t e = launch_tile_ranges(keys, num_keys, ranges, (uint32_t)ntiles, stream);
+    cudaError_t e = launch_tile_ranges(keys, num_keys, ranges, (uint32_t)ntiles, f.flags, stream);
     if (e != cudaSuccess) return e;
     const uint2* r2 = reinterpret_cast<const uint2*>(ranges);
     const float4* s4 = reinterpret_cast<const float4*>(splats);

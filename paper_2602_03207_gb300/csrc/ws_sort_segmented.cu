@@ -41,14 +41,22 @@ constexpr int kMaxSegBits = 24;
 // empty ones included; start[nseg] = n (scan_boundaries over positions 0..n).
 __global__ void __launch_bounds__(256)
 k_seg_bounds(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, uint32_t cap,
-             uint32_t seg_mask, uint32_t nseg, uint32_t* __restrict__ start) {
+             uint32_t seg_mask, uint32_t nseg, uint32_t* __restrict__ start, uint2* __restrict__ ranges,
+             uint32_t ntiles) {
     pdl_wait();
     const int lane = threadIdx.x & 31;
+    const int64_t nt = ranges ? (int64_t)ntiles : 0;
     scan_boundaries<4>(
         keys, min(*num_keys, cap), (int64_t)nseg,
         [seg_mask](uint64_t k) { return (int64_t)((uint32_t)(k >> kSplitBit) & seg_mask); },
         [&](int64_t lo, int64_t hi, uint32_t pos) {
             for (int64_t s = lo + 1 + lane; s <= hi; s += kWarp) start[s] = pos;
+            // the same boundaries as [start, end) per segment: a local sort
+            // keeps every segment in place
+            for (int64_t t = lo + lane; t <= hi && t < nt; t += kWarp) {
+                if (t >= 0 && t < hi) ranges[t].y = pos;
+                if (t > lo) ranges[t].x = pos;
+            }
         });
 }
 
@@ -494,7 +502,8 @@ bool sort_segmented_supported(int64_t key_capacity, int begin_bit, int end_bit) 
 
 cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,
                                   int digit_bits, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
-                                  uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream) {
+                                  uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream,
+                                  uint32_t* ranges, uint32_t ntiles) {
     // Partition by the segment bits: as few passes as digits of at most
     // digit_bits bits allow, their width split evenly (13 segment bits at
     // digit_bits 8 or 9: 7 + 6).
@@ -517,7 +526,8 @@ cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t spans = (key_capacity + 1 + 1023) / 1024;
     e = launch_pdl(k_seg_bounds, dim3((unsigned)(spans < sms * 8 ? spans : sms * 8)), dim3(256), 0, stream,
-                   (const uint64_t*)pk, num_keys, (uint32_t)key_capacity, nseg - 1u, nseg, start);
+                   (const uint64_t*)pk, num_keys, (uint32_t)key_capacity, nseg - 1u, nseg, start,
+                   reinterpret_cast<uint2*>(ranges), ntiles);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_seg_sort, dim3(nseg + (nseg + kSegWarps - 1) / kSegWarps), dim3(kSegThreads), 0, stream, pk, pv,
                    ok, ov, (const uint32_t*)start, num_keys, (uint32_t)key_capacity, nseg, begin_bit);

@@ -38,6 +38,34 @@ def key_end_bit(width, height, tile):
 SORT_FLAGS = {"segmented": capi.WS_CFG_SORT_SEGMENTED, "lsd": 0, "lookback": capi.WS_CFG_SORT_LOOKBACK}
 
 
+def with_flags(cfg, extra):
+    """A copy of a ws_config with more flag bits set."""
+    return capi.Config(cfg.tile, cfg.digit_bits, cfg.dilation, cfg.guard, cfg.flags | int(extra))
+
+
+def sort_frame(obj, ntiles, stream=None):
+    """Sorts obj's pairs. With the segmented sort, ws_sort_tiles also leaves
+    the tile ranges in obj.ranges and the rasterisation is told so
+    (WS_CFG_RANGES_GIVEN); where that sort does not apply (a single tile, or a
+    workspace too small for the segment starts) ws_sort runs and the
+    rasterisation finds the ranges itself. Sets obj.sorted_in_alt and
+    obj.raster_cfg."""
+    if obj.cfg.flags & capi.WS_CFG_SORT_SEGMENTED and getattr(obj, "_tile_sort", True):
+        try:
+            obj.sorted_in_alt = capi.ws_sort_tiles(obj.num_keys, obj.key_capacity, obj.end_bit, obj.keys, obj.vals,
+                                                   obj.keys_alt, obj.vals_alt, obj.cfg, obj.workspace, obj.ranges,
+                                                   ntiles, stream)
+            obj.raster_cfg = with_flags(obj.cfg, capi.WS_CFG_RANGES_GIVEN)
+            return
+        except capi.WsError as e:
+            if e.status != capi.WS_ERR_UNSUPPORTED:
+                raise
+            obj._tile_sort = False
+    obj.sorted_in_alt = capi.ws_sort(obj.num_keys, obj.key_capacity, 0, obj.end_bit, obj.keys, obj.vals,
+                                     obj.keys_alt, obj.vals_alt, obj.cfg, obj.workspace, stream)
+    obj.raster_cfg = obj.cfg
+
+
 def config_flags(flags, sort):
     """ws_config.flags for the user's flags and a sort variant: "segmented"
     (partition by tile, then each tile's depths on chip), "lsd" (full-key
@@ -128,9 +156,7 @@ class Renderer:
                      self.keys, self.vals, self.key_capacity, self.num_keys, self.workspace, stream)
 
     def sort(self, stream=None):
-        self.sorted_in_alt = capi.ws_sort(self.num_keys, self.key_capacity, 0, self.end_bit, self.keys,
-                                          self.vals, self.keys_alt, self.vals_alt, self.cfg,
-                                          self.workspace, stream)
+        sort_frame(self, self.tx * self.ty, stream)
 
     @property
     def sorted_keys(self):
@@ -143,10 +169,10 @@ class Renderer:
     def rasterize(self, cam, stream=None):
         if self.packed:
             capi.ws_rasterize_packed(self.num_keys, self.sorted_keys, self.sorted_vals, self.mean2d_p, self.axes,
-                                     self.rgba, cam, self.cfg, self.ranges, self.image, self.t_final,
+                                     self.rgba, cam, self.raster_cfg, self.ranges, self.image, self.t_final,
                                      self.n_contrib, stream)
             return
-        capi.ws_rasterize(self.num_keys, self.sorted_keys, self.sorted_vals, self.splats, cam, self.cfg,
+        capi.ws_rasterize(self.num_keys, self.sorted_keys, self.sorted_vals, self.splats, cam, self.raster_cfg,
                           self.ranges, self.image, self.t_final, self.n_contrib, stream)
 
     def forward(self, scene, cam_dict, stream=None):
@@ -220,7 +246,7 @@ class Renderer:
         self.sort(stream)
         g = self._grads()
         capi.ws_render_train_l2(self.n, scene["means"], scene["log_scales"], scene["quats"], scene["sh"], cam,
-                                self.cfg, self.num_keys, self.sorted_keys, self.sorted_vals, self.splats, self.rect,
+                                self.raster_cfg, self.num_keys, self.sorted_keys, self.sorted_vals, self.splats, self.rect,
                                 self.offsets, self.tiles_touched, target.contiguous(), self.key_capacity,
                                 self.ranges, self.image, self.t_final, self.n_contrib, g["means"], g["log_scales"],
                                 g["quats"], g["opacity_logits"], g["sh"], self.workspace, stream)

@@ -270,3 +270,58 @@ def test_count_above_capacity_is_clamped(flags):
     for t, b in zip((kt, vt, ka, va), before):
         assert torch.equal(t[cap:], b[cap:])
     assert bool((ws[wsb:] == 0xAB).all())
+
+
+@pytest.mark.parametrize("sizes_seed", [0, 1, 2])
+def test_sort_tiles_writes_the_tile_ranges(sizes_seed):
+    """ws_sort_tiles: the segmented sort's output (bit-identical to ws_sort)
+    plus, for every tile t < ntiles, [start, end) of its keys in the sorted
+    list (empty tiles included), equal to a search of the sorted keys."""
+    import torch
+    from paper_2602_03207_gb300 import capi
+    rng = np.random.default_rng(50 + sizes_seed)
+    ntiles = [1000, 8160, 3][sizes_seed]
+    sizes = [int(x) for x in rng.integers(0, 300, ntiles)]
+    if sizes_seed == 2:
+        sizes = [0, 0, 0]
+    keys, vals = _tile_depth_keys(sizes, rng)
+    n = keys.size
+    end = 31 + max(1, int(np.ceil(np.log2(ntiles))))
+    cap = max(n, 1 << (end - 31) + 1, 4096)
+    kt = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    vt = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    if n:
+        kt[:n] = torch.from_numpy(keys.view(np.int64))
+        vt[:n] = torch.from_numpy(vals.view(np.int32))
+    ka, va = torch.empty_like(kt), torch.empty_like(vt)
+    num = torch.tensor([n, 0, 0, 0], dtype=torch.int32, device="cuda")
+    cfg = capi.config(digit_bits=9, flags=SEG)
+    ws = torch.zeros(capi.ws_workspace_bytes(0, cap, capi.camera(S.small_forward()[1]), cfg), dtype=torch.uint8,
+                     device="cuda")
+    ranges = torch.full((ntiles, 2), -1, dtype=torch.int32, device="cuda")
+    alt = capi.ws_sort_tiles(num, cap, end, kt, vt, ka, va, cfg, ws, ranges, ntiles)
+    torch.cuda.synchronize()
+    k, v = (ka, va) if alt else (kt, vt)
+    ek, ev = oracle.sort_pairs(keys, vals)
+    np.testing.assert_array_equal(k[:n].cpu().numpy().view(np.uint64), ek)
+    np.testing.assert_array_equal(v[:n].cpu().numpy().view(np.uint32), ev)
+    tiles = (ek >> np.uint64(31)).astype(np.int64)
+    t = np.arange(ntiles)
+    expect = np.stack([np.searchsorted(tiles, t, side="left"), np.searchsorted(tiles, t, side="right")], axis=1)
+    np.testing.assert_array_equal(ranges.cpu().numpy(), expect)
+
+
+def test_sort_tiles_rejects_what_the_segmented_sort_cannot_take():
+    """A single-tile key range (end_bit 31) is not segmented: WS_ERR_UNSUPPORTED."""
+    import torch
+    from paper_2602_03207_gb300 import capi
+    num = torch.zeros(4, dtype=torch.int32, device="cuda")
+    k = torch.zeros(16, dtype=torch.int64, device="cuda")
+    v = torch.zeros(16, dtype=torch.int32, device="cuda")
+    ranges = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
+    cfg = capi.config(digit_bits=8, flags=SEG)
+    ws = torch.zeros(capi.ws_workspace_bytes(0, 16, capi.camera(S.small_forward()[1]), cfg), dtype=torch.uint8,
+                     device="cuda")
+    with pytest.raises(capi.WsError) as e:
+        capi.ws_sort_tiles(num, 16, 31, k, v, k, v, cfg, ws, ranges, 1)
+    assert e.value.status == capi.WS_ERR_UNSUPPORTED
