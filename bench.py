@@ -514,9 +514,11 @@ def run_ours(args):
     stage_ms = {s: sum(v) / stage_steps for s, v in per.items()}
     stage_p99 = {s: float(np.percentile(v, 99)) for s, v in per.items()}
 
-    # end to end through the public API (render.FramePipeline): every frame
-    # uploads its scene from pinned host memory and reads its image back;
-    # frame i+1's upload overlaps frame i's render and read-back
+    # end to end through the C ABI (ws_render_frame_host, driven by
+    # render.FramePipeline): every frame copies its scene from pinned host
+    # memory and its image back to pinned host memory inside the call; two
+    # slots on two streams, so frame i+1's upload overlaps frame i's render
+    # and read-back
     e2e = None
     if not args.no_e2e:
         host = {k: torch.from_numpy(np.ascontiguousarray(scene_np[k])).pin_memory() for k in render.SCENE_KEYS}
@@ -546,7 +548,8 @@ def run_ours(args):
         t2 = max_over_ranks(a.elapsed_time(b) / 1e3, dist if world > 1 else None, dev)
         e2e = {"value": whole_job_rate(k2, world, t2), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k2,
-               "api": "render.FramePipeline (upload of frame i+1 overlaps render + read-back of frame i)"}
+               "api": "C ABI ws_render_frame_host per frame (host scene -> device, the four stages, image -> "
+                      "host), two slots on two streams: frame i+1's upload overlaps frame i's render"}
         del pipe
 
     result = None

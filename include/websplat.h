@@ -276,6 +276,36 @@ ws_status ws_rasterize(const uint32_t *num_keys, const uint64_t *keys, const uin
                        uint32_t *ranges, float *image, float *t_final, uint32_t *n_contrib,
                        void *stream);
 
+/* The device buffers of one frame (all caller-allocated, 16-byte aligned):
+ * the scene's arrays (n entries each, the input layouts) and everything the
+ * four calls above read and write, sized as those calls state for n
+ * Gaussians, key_capacity pairs and the camera's resolution and tile grid;
+ * workspace of ws_workspace_bytes(n, key_capacity, cam, cfg) bytes. */
+typedef struct ws_frame_buffers {
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+    float *splats, *depth;
+    uint16_t *rect;
+    uint32_t *tiles_touched, *offsets;
+    uint64_t *keys, *keys_alt;
+    uint32_t *vals, *vals_alt, *num_keys, *ranges;
+    float *image, *t_final;
+    uint32_t *n_contrib;
+    void *workspace;
+    int64_t key_capacity;
+} ws_frame_buffers;
+
+/* One frame from a scene in host memory to an image in host memory, all
+ * enqueued on `stream`: the five scene arrays are copied host -> device into
+ * buf (cudaMemcpyAsync), then ws_preprocess, ws_cull, the sort (ws_sort_tiles
+ * where the segmented sort applies, else ws_sort) and ws_rasterize run, and
+ * the image is copied device -> host into h_image (H x W x 3 float32). The
+ * copies are asynchronous only from page-locked host memory; the call never
+ * synchronises the host, so read h_image after synchronising the stream, and
+ * check the capacity flag with ws_read_status. Errors as the calls it makes. */
+ws_status ws_render_frame_host(int64_t n, const float *h_means, const float *h_log_scales, const float *h_quats,
+                               const float *h_opacity_logits, const float *h_sh, const ws_camera *cam,
+                               const ws_config *cfg, const ws_frame_buffers *buf, float *h_image, void *stream);
+
 /* Packed-record variant of ws_preprocess (§3.2 packs each splat's colour and
  * opacity into one RGBA8 word and its ellipse axes into two words of
  * binary16 halves). Same inputs and the same culling as ws_preprocess; per

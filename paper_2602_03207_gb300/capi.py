@@ -34,7 +34,7 @@ EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_prepr
            "ws_rasterize_backward", "ws_read_status", "ws_batch_max_views", "ws_batch_workspace_bytes",
            "ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
            "ws_image_residual", "ws_sort_test_stalled_tile", "ws_render_train_l2", "ws_render_train_l2_batch",
-           "ws_sort_tiles")
+           "ws_sort_tiles", "ws_render_frame_host")
 
 
 class WsError(RuntimeError):
@@ -48,6 +48,13 @@ class Camera(C.Structure):
     _fields_ = [("viewmat", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
                 ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32), ("znear", C.c_float),
                 ("bg", C.c_float * 3)]
+
+
+class FrameBuffers(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in (
+        "means", "log_scales", "quats", "opacity_logits", "sh", "splats", "depth", "rect", "tiles_touched",
+        "offsets", "keys", "keys_alt", "vals", "vals_alt", "num_keys", "ranges", "image", "t_final",
+        "n_contrib", "workspace")] + [("key_capacity", C.c_int64)]
 
 
 class Config(C.Structure):
@@ -104,6 +111,8 @@ def lib():
             L.ws_sort_test_stalled_tile.restype = I32
             L.ws_sort_tiles.argtypes = [P, I64, I32, P, P, P, P, cfg_p, P, P, I64, C.POINTER(I32), P]
             L.ws_sort_tiles.restype = I32
+            L.ws_render_frame_host.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, C.POINTER(FrameBuffers), P, P]
+            L.ws_render_frame_host.restype = I32
             L.ws_sort_noalloc.argtypes = [P, I64, I32, I32, P, P, P, P, I32, C.POINTER(I32), P]
             L.ws_sort_noalloc.restype = I32
             L.ws_sort_noalloc_max_keys.restype = I64
@@ -338,3 +347,25 @@ def ws_render_train_l2_batch(n, means, log_scales, quats, sh, cams_arr, cfg, num
         _ptr(num_keys), _ptr(keys), _ptr(vals), _ptr(splats), _ptr(rect), _ptr(offsets), _ptr(tiles_touched),
         _ptr(target), int(key_capacity), _ptr(ranges), _ptr(image), _ptr(t_final), _ptr(n_contrib), _ptr(d_means),
         _ptr(d_log_scales), _ptr(d_quats), _ptr(d_opacity_logits), _ptr(d_sh), _ptr(workspace), _stream(stream)))
+
+
+def frame_buffers(**ptrs) -> FrameBuffers:
+    """ws_frame_buffers from device tensors (by field name) and key_capacity."""
+    b = FrameBuffers()
+    for name, _ in FrameBuffers._fields_:
+        if name == "key_capacity":
+            b.key_capacity = int(ptrs["key_capacity"])
+        else:
+            setattr(b, name, _ptr(ptrs[name]))
+    return b
+
+
+def ws_render_frame_host(n, h_scene, cam, cfg, buffers, h_image, stream=None):
+    """One frame from host scene arrays (dict of CPU tensors, ideally pinned)
+    into a host image tensor (H, W, 3), on `stream`; asynchronous."""
+    def hp(t):
+        return t.data_ptr() if t.numel() else None
+    _check("ws_render_frame_host", lib().ws_render_frame_host(
+        int(n), hp(h_scene["means"]), hp(h_scene["log_scales"]), hp(h_scene["quats"]),
+        hp(h_scene["opacity_logits"]), hp(h_scene["sh"]), C.byref(cam), C.byref(cfg), C.byref(buffers),
+        hp(h_image), _stream(stream)))

@@ -297,6 +297,55 @@ ws_status ws_rasterize(const uint32_t* num_keys, const uint64_t* keys, const uin
                                             image, t_final, n_contrib, static_cast<cudaStream_t>(stream)));
 }
 
+ws_status ws_render_frame_host(int64_t n, const float* h_means, const float* h_log_scales, const float* h_quats,
+                               const float* h_opacity_logits, const float* h_sh, const ws_camera* cam,
+                               const ws_config* cfg, const ws_frame_buffers* b, float* h_image, void* stream) {
+    if (!b || !h_image || n < 0 || n >= (int64_t(1) << 32) || !valid_camera(cam) || !valid_config(cfg))
+        return WS_ERR_INVALID_ARG;
+    const void* hp[] = {h_means, h_log_scales, h_quats, h_opacity_logits, h_sh};
+    if (n > 0)
+        for (const void* p : hp)
+            if (!p) return WS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n > 0) {
+        const size_t nn = (size_t)n * sizeof(float);
+        const struct { void* dst; const void* src; size_t bytes; } up[] = {
+            {b->means, h_means, 3 * nn}, {b->log_scales, h_log_scales, 3 * nn}, {b->quats, h_quats, 4 * nn},
+            {b->opacity_logits, h_opacity_logits, nn}, {b->sh, h_sh, 48 * nn}};
+        for (const auto& c : up) {
+            if (!c.dst) return WS_ERR_INVALID_ARG;
+            if (cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return WS_ERR_CUDA;
+        }
+    }
+    ws_status st = ws_preprocess(n, b->means, b->log_scales, b->quats, b->opacity_logits, b->sh, cam, cfg,
+                                 b->splats, b->depth, b->rect, b->tiles_touched, stream);
+    if (st != WS_OK) return st;
+    st = ws_cull(n, b->tiles_touched, b->rect, b->depth, cam, cfg, b->offsets, b->keys, b->vals, b->key_capacity,
+                 b->num_keys, b->workspace, stream);
+    if (st != WS_OK) return st;
+    const int64_t tiles = (int64_t)((cam->width + cfg->tile - 1) / cfg->tile) * ((cam->height + cfg->tile - 1) / cfg->tile);
+    int end_bit = 31;
+    while ((int64_t(1) << (end_bit - 31)) < tiles) ++end_bit;
+    if (end_bit == 31) end_bit = 32;
+    ws_config rc = *cfg;
+    int32_t in_alt = 0;
+    st = WS_ERR_UNSUPPORTED;
+    if (cfg->flags & WS_CFG_SORT_SEGMENTED) {
+        st = ws_sort_tiles(b->num_keys, b->key_capacity, end_bit, b->keys, b->vals, b->keys_alt, b->vals_alt, cfg,
+                           b->workspace, b->ranges, tiles, &in_alt, stream);
+        if (st == WS_OK) rc.flags |= WS_CFG_RANGES_GIVEN;
+    }
+    if (st == WS_ERR_UNSUPPORTED)
+        st = ws_sort(b->num_keys, b->key_capacity, 0, end_bit, b->keys, b->vals, b->keys_alt, b->vals_alt, cfg,
+                     b->workspace, &in_alt, stream);
+    if (st != WS_OK) return st;
+    st = ws_rasterize(b->num_keys, in_alt ? b->keys_alt : b->keys, in_alt ? b->vals_alt : b->vals, b->splats, cam,
+                      &rc, b->ranges, b->image, b->t_final, b->n_contrib, stream);
+    if (st != WS_OK) return st;
+    const size_t img = (size_t)cam->width * cam->height * 3 * sizeof(float);
+    return cuda_status(cudaMemcpyAsync(h_image, b->image, img, cudaMemcpyDeviceToHost, s));
+}
+
 ws_status ws_preprocess_packed(int64_t n, const float* means, const float* log_scales, const float* quats,
                                const float* opacity_logits, const float* sh, const ws_camera* cam,
                                const ws_config* cfg, float* mean2d, uint32_t* axes, uint32_t* rgba, float* depth,

@@ -278,50 +278,49 @@ class Renderer:
 
 
 class FramePipeline:
-    """Frames whose scene and image live in host memory: every frame uploads
-    its scene from (pinned) host memory and reads its image back. Each of
-    `slots` slots owns a Renderer, a device copy of the scene and a stream;
-    uploads run in frame order on one upload stream, so frame i+1's upload
-    overlaps frame i's render and read-back and a stream of frames runs at
-    the pace of the host-device link rather than upload + render + read-back
-    in series. A slot is reused only after its previous frame's read-back has
-    finished. Everything is asynchronous; synchronize() waits for all frames
-    and checks each renderer's status."""
+    """Frames whose scene and image live in host memory, each rendered by one
+    C-ABI call (ws_render_frame_host: the scene's host -> device copies, the
+    four stages and the image's device -> host copy, on one stream). Each of
+    `slots` slots owns a Renderer, the device copy of the scene and a stream,
+    and frames go to the slots in turn, so frame i+1's upload overlaps frame
+    i's render and read-back and a stream of frames runs at the pace of the
+    host-device link rather than upload + render + read-back in series. A
+    slot's next frame follows its previous one on its stream. Everything is
+    asynchronous; synchronize() waits for all frames and checks each
+    renderer's status."""
 
     def __init__(self, n, width, height, slots=2, device="cuda", **renderer_kw):
         self.device = torch.device(device)
+        self.n = int(n)
         self.slots = []
         for _ in range(int(slots)):
-            self.slots.append({"r": Renderer(n, width, height, device=self.device, **renderer_kw),
-                               "scene": None, "stream": torch.cuda.Stream(self.device), "done": None})
-        self.upload = torch.cuda.Stream(self.device)
+            r = Renderer(n, width, height, device=self.device, **renderer_kw)
+            scene = {k: torch.empty(shape, dtype=torch.float32, device=self.device)
+                     for k, shape in (("means", (max(n, 1), 3)), ("log_scales", (max(n, 1), 3)),
+                                      ("quats", (max(n, 1), 4)), ("opacity_logits", (max(n, 1),)),
+                                      ("sh", (max(n, 1), 16, 3)))}
+            self.slots.append({"r": r, "scene": scene, "stream": torch.cuda.Stream(self.device), "buf": None})
         self.count = 0
 
     def streams(self):
-        return [self.upload] + [s["stream"] for s in self.slots]
+        return [s["stream"] for s in self.slots]
 
     def submit(self, host_scene, cam_dict, host_image):
-        """Queue one frame: upload host_scene (dict of CPU tensors, ideally
-        pinned), render with cam_dict, copy the image into host_image (a CPU
-        float32 tensor of shape (H, W, 3), ideally pinned). Returns at once."""
+        """Queue one frame: host_scene (dict of CPU float32 tensors in the
+        input layouts, ideally pinned), cam_dict, host_image (a CPU float32
+        tensor (H, W, 3), ideally pinned). Returns at once."""
         s = self.slots[self.count % len(self.slots)]
         self.count += 1
-        if s["scene"] is None:
-            s["scene"] = {k: torch.empty(tuple(host_scene[k].shape), dtype=torch.float32, device=self.device)
-                          for k in SCENE_KEYS}
-        if s["done"] is not None:
-            self.upload.wait_event(s["done"])
-        with torch.cuda.stream(self.upload):
-            for k in SCENE_KEYS:
-                s["scene"][k].copy_(host_scene[k], non_blocking=True)
-            up = torch.cuda.Event()
-            up.record(self.upload)
-        s["stream"].wait_event(up)
-        with torch.cuda.stream(s["stream"]):
-            s["r"].forward(s["scene"], cam_dict)
-            host_image.copy_(s["r"].image, non_blocking=True)
-            s["done"] = torch.cuda.Event()
-            s["done"].record(s["stream"])
+        r = s["r"]
+        cam = capi.camera(cam_dict)
+        if s["buf"] is None:
+            r._ensure_workspace(cam)
+            s["buf"] = capi.frame_buffers(
+                **s["scene"], splats=r.splats, depth=r.depth, rect=r.rect, tiles_touched=r.tiles_touched,
+                offsets=r.offsets, keys=r.keys, keys_alt=r.keys_alt, vals=r.vals, vals_alt=r.vals_alt,
+                num_keys=r.num_keys, ranges=r.ranges, image=r.image, t_final=r.t_final, n_contrib=r.n_contrib,
+                workspace=r.workspace, key_capacity=r.key_capacity)
+        capi.ws_render_frame_host(self.n, host_scene, cam, r.cfg, s["buf"], host_image, s["stream"])
 
     def synchronize(self):
         torch.cuda.synchronize(self.device)

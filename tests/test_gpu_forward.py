@@ -325,8 +325,10 @@ def test_ply_scene_renders_like_the_original(tmp_path):
 
 
 def test_frame_pipeline_matches_renderer():
-    """Frames from host memory through render.FramePipeline (uploads
-    overlapping renders on two slots) are bit-identical to Renderer frames."""
+    """Frames from host memory through render.FramePipeline (one C-ABI
+    ws_render_frame_host call per frame: the scene's upload, the four stages
+    and the image's read-back; two slots, so uploads overlap renders) are
+    bit-identical to Renderer frames."""
     import torch
     from paper_2602_03207_gb300 import render
     scene, _ = S.small_forward()
