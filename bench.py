@@ -34,9 +34,10 @@ WORKLOADS = {
 METRIC = "1080p frames/s at 1M splats"
 METRICS = {"hd": METRIC, "uhd": "2160p frames/s at 6M splats"}
 # DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernel on the hd workload (profiles/kernels_hd_1080p_1M.md); to be reset
-# to None whenever that kernel changes.
-KERNEL_TRAFFIC = {("k_blend", 16): 51_419_648 + 16_329_216}
+# kernel (profiles/kernels_hd_1080p_1M.md: k_blend on the 1080p frame;
+# profiles/kernels_bwd_720p_500k.md: k_blend_bwd on the 720p training step);
+# to be reset to None whenever that kernel changes.
+KERNEL_TRAFFIC = {("k_blend", 16): 51_982_592 + 11_175_424, ("k_blend_bwd", 16): 49_810_432 + 1_607_168}
 STAGES = ("preprocess", "cull", "sort", "rasterize")
 
 
@@ -822,7 +823,8 @@ def train_block(args, dev, min_timed_s=1.0, stage_steps=100):
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "roofline": {"kernel": f"k_blend_bwd<{r.tile}> (timed span: ws_rasterize_backward)", "bound": "alu",
                          "alg_evals": int(evals), "achieved": round(ach, 3), "peak": round(peak, 2),
-                         "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                         "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                         "traffic": KERNEL_TRAFFIC.get(("k_blend_bwd", r.tile)),
                          "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"},
             "clocks": clk.summary()}
 
