@@ -985,14 +985,17 @@ def batch_block(args, dev, min_timed_s=1.0, plain_min_s=0.5):
 
 def uhd_block(args, dev, frames=16):
     """The 3840x2160 / 6,000,000-Gaussian workload: per-stage times and peak
-    device memory of a frame with and without culling (no sigma < 1/255 cull
-    and no viewport test), over the 8 orbit poses."""
+    device memory of a frame over the 8 orbit poses, for the full pipeline,
+    each of the three ablations, and both culls off at once (no sigma < 1/255
+    cull and no viewport test)."""
     import torch
     from paper_2602_03207_gb300 import capi, render
     scene_np, cams = workload("uhd")
     scene = render.scene_to_device(scene_np, dev)
     tab = ablation_table(scene, cams, args.tile, args.digit_bits, dev, frames=frames,
-                         variants={"full": 0, "no-cull": capi.WS_CFG_NO_OPACITY_CULL | capi.WS_CFG_NO_AABB_CULL})
+                         variants={"full": 0, "-cull": capi.WS_CFG_NO_AABB_CULL,
+                                   "-radius": capi.WS_CFG_FIXED_RADIUS, "-opacity": capi.WS_CFG_NO_OPACITY_CULL,
+                                   "no-cull": capi.WS_CFG_NO_OPACITY_CULL | capi.WS_CFG_NO_AABB_CULL})
     del scene
     torch.cuda.empty_cache()
     return {"workload": WORKLOADS["uhd"]["desc"], "frames_per_variant": frames, "variants": tab,
