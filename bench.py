@@ -547,11 +547,11 @@ def run_ours(args):
         b.record(main)
         pipe.synchronize()
         t2 = max_over_ranks(a.elapsed_time(b) / 1e3, dist if world > 1 else None, dev)
+        del pipe
         e2e = {"value": whole_job_rate(k2, world, t2), "unit": "frames/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": k2,
+               "d2h_bytes_per_step": d2h, "steps": k2, "link": link_bandwidth(host, himg[0], dev),
                "api": "C ABI ws_render_frame_host per frame (host scene -> device, the four stages, image -> "
                       "host), two slots on two streams: frame i+1's upload overlaps frame i's render"}
-        del pipe
 
     result = None
     if rank == 0:
@@ -566,6 +566,32 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def link_bandwidth(host, himg, dev, reps=10):
+    """Plain copies of one frame's bytes over the host-device link (the scene
+    to the device, the image back), GB/s: the ceiling of the end-to-end rate."""
+    import torch
+    dsc = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    dimg = torch.empty_like(himg, device=dev)
+    s = torch.cuda.Stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with torch.cuda.stream(s):
+        for rep in range(reps + 1):
+            if rep == 1:
+                ev[0].record(s)
+            for k, v in host.items():
+                dsc[k].copy_(v, non_blocking=True)
+        ev[1].record(s)
+        for _ in range(reps):
+            himg.copy_(dimg, non_blocking=True)
+        ev[2].record(s)
+    torch.cuda.synchronize(dev)
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) * reps
+    d2h = himg.numel() * himg.element_size() * reps
+    return {"h2d_gbs": round(h2d / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e9, 1),
+            "d2h_gbs": round(d2h / (ev[1].elapsed_time(ev[2]) / 1e3) / 1e9, 1),
+            "note": "plain pinned copies of the frame's scene and image, timed on their own"}
 
 
 def frame_config(args, world):

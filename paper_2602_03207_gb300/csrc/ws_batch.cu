@@ -92,7 +92,7 @@ k_preprocess_batch(int64_t n, const float* __restrict__ means, const float* __re
 }
 
 template <int TS>
-__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS)
+__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS, blend_min_blocks<TS>())
 k_blend_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, int64_t n,
               const float4* __restrict__ splats, const FrameTable ft,
               float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {

@@ -204,7 +204,7 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
 }
 
 template <int TS>
-__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS)
+__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS, blend_min_blocks<TS>())
 k_blend_packed(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                const float2* __restrict__ mean2d, const uint2* __restrict__ axes,
                const uint32_t* __restrict__ rgba, const Frame f, float* __restrict__ image,

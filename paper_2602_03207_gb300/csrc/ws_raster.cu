@@ -49,7 +49,7 @@ k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ nu
 }
 
 template <int TS>
-__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS)
+__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS, blend_min_blocks<TS>())
 k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, const float4* __restrict__ splats,
         const Frame f, float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
     pdl_wait();

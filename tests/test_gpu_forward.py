@@ -203,12 +203,13 @@ def test_frames_are_bitwise_deterministic():
 
 def test_hd_workload_sampled():
     """The 1,000,000-Gaussian 1920x1080 workload in the benchmark's launch
-    configuration (16x16 tiles, 8-bit digits): every Gaussian's
-    pre-processing, the whole pair list and sort, and the image on 96
-    sampled tiles (the densest 32 plus 64 seeded ones) against the oracle."""
+    configuration (16x16 tiles, 9-bit digits, the segmented sort writing the
+    tile ranges): every Gaussian's pre-processing, the whole pair list and
+    sort, and the image on 96 sampled tiles (the densest 32 plus 64 seeded
+    ones) against the oracle."""
     scene = S.hd_scene()
     cam = S.hd_camera(0)
-    r = gpu_frame(scene, cam)
+    r = gpu_frame(scene, cam, digit_bits=9)
     g = fetch(r)
     tx, ty = (1920 + 15) // 16, (1080 + 15) // 16
     counts = g["ranges"][:, 1] - g["ranges"][:, 0]
@@ -232,10 +233,11 @@ def test_uhd_workload_sampled():
     """The 6,000,000-Gaussian 3840x2160 workload (pose 3, whose densest tile
     holds 4,389 pairs: the segmented sort's global-memory path): every
     Gaussian's pre-processing, the whole pair list and sort, and the image on
-    the densest 32 plus 64 seeded tiles against the oracle."""
+    the densest 32 plus 64 seeded tiles against the oracle, in the
+    benchmark's launch configuration (16x16 tiles, 9-bit digits)."""
     scene = S.uhd_scene()
     cam = S.uhd_camera(3)
-    r = gpu_frame(scene, cam)
+    r = gpu_frame(scene, cam, digit_bits=9)
     g = fetch(r)
     tx, ty = (3840 + 15) // 16, (2160 + 15) // 16
     counts = g["ranges"][:, 1] - g["ranges"][:, 0]
