@@ -41,7 +41,10 @@
  *   [4] a [5] b [6] c                    conic Sigma'^{-1} = [[a, b], [b, c]]
  *   [7] sigma                            opacity
  *   [8] r [9] g [10] b                   colour
- *   [11] 0
+ *   [11] t                               tan(theta / 2), theta in [-pi/2, pi/2]
+ *        the angle of the major axis of Sigma' = conic^{-1} (0 for a circle);
+ *        the backward sums each pair's conic derivatives in the basis
+ *        e1 = ((1 - t^2), 2 t) / (1 + t^2), e2 = e1 turned by +90 degrees
  * A culled Gaussian's record is all zeros.
  */
 #ifndef WEBSPLAT_H
@@ -103,6 +106,8 @@ typedef struct ws_config {
 #define WS_CFG_SORT_SEGMENTED 16u /* ws_sort: partition by bits [31, end) then sort each segment on chip */
 #define WS_CFG_PERSISTENT 32u     /* ws_render_train_l2_batch: one persistent grid over every (view, tile) */
 #define WS_CFG_RANGES_GIVEN 64u   /* rasterize / train calls: `ranges` already holds the tile ranges (ws_sort_tiles) */
+#define WS_CFG_BOX_MASKS 128u     /* backward / train calls: visit every 4x4 sub-block of a splat's bounding box,
+                                     not only those that its ellipse meets (same results; an ablation and a check) */
 
 /* Library ABI version (WS_ABI_VERSION of the build). */
 int32_t ws_abi_version(void);
@@ -372,7 +377,8 @@ ws_status ws_render_quads(int64_t n, const float *splats, const float *depth, co
  * channel clamped at 0.
  * Deterministic, without float atomics: each tile walks its list back to
  * front from t_final / n_contrib, reduces each pair's 9 partial derivatives
- * (centre 2, conic 3, sigma 1 (times sigma), colour 3) inside the block in a fixed order
+ * (centre 2, conic 3 in the splat's axis basis (record word 11), sigma 1
+ * (times sigma), colour 3) inside the block in a fixed order
  * and writes them to the pair's emission slot offsets[g] + k in the
  * workspace; each Gaussian then sums its slots in order and applies the
  * adjoint of its pre-processing. Bitwise reproducible.

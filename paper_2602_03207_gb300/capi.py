@@ -26,6 +26,7 @@ WS_CFG_NO_OPACITY_CULL, WS_CFG_NO_AABB_CULL, WS_CFG_SORT_LOOKBACK, WS_CFG_FIXED_
 WS_CFG_SORT_SEGMENTED = 16
 WS_CFG_PERSISTENT = 32
 WS_CFG_RANGES_GIVEN = 64
+WS_CFG_BOX_MASKS = 128
 WS_ABI_VERSION = 2
 WS_SPLAT_FLOATS = 12  # floats per splat record: centre hi/lo (4), conic (3), sigma, colour (3), 0
 

@@ -122,7 +122,7 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
 #pragma unroll
             for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
         glogit = pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
-        splat_adjoint(f, X, q4, ls, pr, gm, gls, gq);
+        splat_adjoint(f, X, q4, ls, pr, cl.w, gm, gls, gq);  // cl.w: the axis basis's t
     }
 
     // SH colour adjoint; gradients staged back through shared memory for

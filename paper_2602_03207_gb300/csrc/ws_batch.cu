@@ -220,8 +220,8 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
         const float sig = __ldg(splats + kSplatVec4 * o + 1).w;  // sigma (the same in every view)
         glogit += pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
         const Frame& f = ft.f[v];
-        splat_adjoint(f, X, q4, ls, pr, gm, gls, gq);
-        const float4 cl = __ldg(splats + kSplatVec4 * o + 2);
+        const float4 cl = __ldg(splats + kSplatVec4 * o + 2);  // colour and the axis basis's t
+        splat_adjoint(f, X, q4, ls, pr, cl.w, gm, gls, gq);
         const float col[3] = {cl.x, cl.y, cl.z};
         sh_adjoint(f, X, stage + lane * kShPad, col, pr, gm, gsh, true);
     }

@@ -21,14 +21,32 @@ constexpr int blend_min_blocks() { return TS == 8 ? 16 : (TS == 16 ? 8 : 4); }
 // Shared-memory record of one staged splat (48 bytes):
 //   geo  = tile-relative centre x, y; conic premultiplied A = -log2(e) a / 2,
 //          B = -log2(e) b
-//   geo2 = C = -log2(e) c / 2, L = log2(sigma); raw conic a, b
-//   col  = r, g, b; raw conic c
+//   geo2 = C = -log2(e) c / 2, L = log2(sigma); the splat's axis basis
+//          e1 = (ct, st) (axis_basis; staged for the backward only)
+//   col  = r, g, b; 0
 // The forward reads geo, geo2.xy and col.xyz; the backward everything.
 struct SplatRec {
     float4 geo;
     float4 geo2;
     float4 col;
 };
+
+// Staged records sit in groups of 33: slot 33 g holds a null splat (zero
+// conic, L = -inf, so its log-alpha is -inf and it is never composited) and
+// slots 33 g + 1 .. 33 g + 32 the splats 32 g .. 32 g + 31, so that a
+// half-warp with nothing left to visit in a group of 32 reads the null splat
+// at index 0 of the group (__ffs of an empty bit set) and needs no select.
+__device__ __forceinline__ int rec_slot(int j) { return j + (j >> 5) + 1; }
+__host__ __device__ constexpr int rec_slots(int batch) { return batch + batch / 32 + 1; }
+
+// Writes the null splat of every group of a staging area of `batch` splats.
+__device__ __forceinline__ void init_null_splats(SplatRec* s_rec, int batch) {
+    for (int g = threadIdx.x; g <= (batch - 1) / 32; g += blockDim.x) {
+        s_rec[33 * g].geo = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_rec[33 * g].geo2 = make_float4(0.f, -INFINITY, 0.f, 0.f);
+        s_rec[33 * g].col = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
 
 // Per-splat inputs of the blend, read from the splat records of
 // ws_preprocess (three 16-byte loads of one 48-byte record): the double-float
@@ -145,7 +163,8 @@ __device__ __forceinline__ MaskT ellipse_subblock_mask(float gx, float gy, float
 // ellipse is left out; a sub-block visited without need adds w = 0. The
 // ellipse's mask costs more arithmetic per staged splat and saves visits
 // (13 % of them on the 1080p / 1M frame): a gain where a visit is dear (the
-// backward), not in the forward.
+// backward), not in the forward. WS_CFG_BOX_MASKS takes the box's mask
+// everywhere; the results are the same bits either way.
 template <int TS, bool ELLIPSE, typename Splats>
 __device__ __forceinline__ void stage_splat(const Frame& f, float ox, float oy, const Splats& sp, uint32_t g,
                                             SplatRec* dst, typename TileGeom<TS>::Mask& mask) {
@@ -154,16 +173,18 @@ __device__ __forceinline__ void stage_splat(const Frame& f, float ox, float oy, 
     sp.load(g, ox, oy, gx, gy, a, b, c, op, col);
     const float L = lg2_approx(op);
     // the record first: its registers are free before the mask's arithmetic
+    float ct = 0.f, st = 0.f;
+    if (ELLIPSE) axis_basis(col.w, ct, st);
     dst->geo = make_float4(gx, gy, -0.5f * kLog2e * a, -kLog2e * b);
-    dst->geo2 = make_float4(-0.5f * kLog2e * c, L, a, b);
-    dst->col = make_float4(col.x, col.y, col.z, c);
+    dst->geo2 = make_float4(-0.5f * kLog2e * c, L, ct, st);
+    dst->col = make_float4(col.x, col.y, col.z, 0.f);
     const float qc = (f.flags & WS_CFG_FIXED_RADIUS) ? 2.f * kLn255 : fmaxf(0.f, kTwoLn2 * (L - kLog2AlphaMin));
     const float qm = fmaf(qc, 1.001f, 1e-3f);
     const float rdet = rcp_approx(fmaf(a, c, -b * b));
     const float ex = sqrt_approx(qm * c * rdet) * 1.0001f + 1e-3f;
     const float ey = sqrt_approx(qm * a * rdet) * 1.0001f + 1e-3f;
     using M = typename TileGeom<TS>::Mask;
-    if (ELLIPSE)
+    if (ELLIPSE && !(f.flags & WS_CFG_BOX_MASKS))
         mask = ellipse_subblock_mask<TileGeom<TS>::SPR, M>(gx, gy, a, b, c, qm, rdet, ey, fmaf(ex, 1e-4f, 1e-3f));
     else
         mask = box_subblock_mask<TileGeom<TS>::SPR, M>(gx - ex, gx + ex, gy - ey, gy + ey);
@@ -191,9 +212,11 @@ struct FwdPixels {
     // 1-based for n_contrib). Each half-warp walks the batch 32 splats at a
     // time and visits only the splats whose mask has its own sub-block, in
     // list order; the two halves run in lockstep for max(visits of either
-    // half) steps, the idle half adding w = 0, which leaves C and T bit for
-    // bit unchanged, so per pixel the compositing order and arithmetic are
-    // those of a plain front-to-back loop.
+    // half) steps, the idle half visiting its group's null splat (w = 0,
+    // which leaves C and T bit for bit unchanged), so per pixel the
+    // compositing order and arithmetic are those of a plain front-to-back
+    // loop. The last composited position is noted per group (1-based within
+    // the group) and made a list position once at the group's end.
     __device__ __forceinline__ void batch(const SplatRec* s_rec, const typename G::Mask* s_mask, int cnt,
                                           uint32_t rel0, int lane) {
         const int half = lane >> 4;
@@ -206,24 +229,26 @@ struct FwdPixels {
                 const uint32_t bb = __ballot_sync(kFull, (uint32_t)(m >> (sb[k] + 1)) & 1u);
                 uint32_t bits = half ? bb : ba;
                 const int steps = max(__popc(ba), __popc(bb));
+                const SplatRec* grp = s_rec + base + (base >> 5);  // grp[0]: the null splat
+                int lastk = 0;
                 for (int it = 0; it < steps; ++it) {
-                    const bool act = bits != 0u;
-                    const int j = base + (act ? __ffs(bits) - 1 : 0);
+                    const int q = __ffs(bits);  // 0 once this half has no visit left
                     bits &= bits - 1u;
-                    const float4 geo = s_rec[j].geo;
-                    const float2 geo2 = *reinterpret_cast<const float2*>(&s_rec[j].geo2);
+                    const float4 geo = grp[q].geo;
+                    const float2 geo2 = *reinterpret_cast<const float2*>(&grp[q].geo2);
                     const float dx = px[k] - geo.x, dy = py[k] - geo.y;
                     const float e = splat_log2_alpha(dx, dy, geo.z, geo.w, geo2.x, geo2.y);
-                    const bool keep = act && e >= kLog2AlphaMin;
+                    const bool keep = e >= kLog2AlphaMin;
                     const float alpha = fminf(kAlphaMax, ex2_approx(e));
                     const float w = keep ? alpha * T[k] : 0.f;
-                    const float4 col = s_rec[j].col;
+                    const float4 col = grp[q].col;
                     C0[k] = fmaf(col.x, w, C0[k]);
                     C1[k] = fmaf(col.y, w, C1[k]);
                     C2[k] = fmaf(col.z, w, C2[k]);
                     T[k] = T[k] - w;
-                    last[k] = keep ? rel0 + j : last[k];
+                    lastk = keep ? q : lastk;
                 }
+                if (lastk) last[k] = rel0 + (uint32_t)(base + lastk - 1);
             }
         }
     }
@@ -292,7 +317,7 @@ struct BwdPixels {
                         for (int c = 0; c < kPart; ++c) acc[c] = 0.f;
                         bool any = false;
                         if (act && pos < last[k]) {
-                            const SplatRec r = s_rec[j];
+                            const SplatRec r = s_rec[rec_slot(j)];
                             const float dx = px[k] - r.geo.x, dy = py[k] - r.geo.y;
                             const float e = splat_log2_alpha(dx, dy, r.geo.z, r.geo.w, r.geo2.x, r.geo2.y);
                             if (e >= kLog2AlphaMin) {
@@ -314,12 +339,17 @@ struct BwdPixels {
                                 if (raw < kAlphaMax) {
                                     acc[5] = raw * dalpha;
                                     const float dp = alpha * dalpha;
-                                    const float ca = r.geo2.z, cb = r.geo2.w, cc2 = r.col.w;
-                                    acc[0] = dp * (ca * dx + cb * dy);
-                                    acc[1] = dp * (cb * dx + cc2 * dy);
-                                    acc[2] = dp * (-0.5f * dx * dx);
-                                    acc[3] = dp * (-dx * dy);
-                                    acc[4] = dp * (-0.5f * dy * dy);
+                                    // d/dmean = dp C d with C = -(2A, B; B, 2C) / log2(e)
+                                    const float dpl = -kLn2 * dp;
+                                    acc[0] = dpl * fmaf(2.f * r.geo.z, dx, r.geo.w * dy);
+                                    acc[1] = dpl * fmaf(r.geo.w, dx, 2.f * r.geo2.x * dy);
+                                    // conic derivatives in the splat's axis basis
+                                    const float ct = r.geo2.z, st = r.geo2.w;
+                                    const float u = fmaf(ct, dx, st * dy), v = fmaf(ct, dy, -st * dx);
+                                    const float hdp = -0.5f * dp;
+                                    acc[2] = hdp * (u * u);
+                                    acc[3] = -dp * (u * v);
+                                    acc[4] = hdp * (v * v);
                                 }
                             }
                         }
@@ -435,7 +465,7 @@ __device__ __forceinline__ void stage_batch(const Frame& f, float ox, float oy, 
     for (int j = threadIdx.x; j < cnt; j += TileGeom<TS>::THREADS) {
         const uint32_t g = __ldg(vals + start + j);
         typename TileGeom<TS>::Mask m;
-        stage_splat<TS, WITH_SLOT>(f, ox, oy, sp, g, s_rec + j, m);
+        stage_splat<TS, WITH_SLOT>(f, ox, oy, sp, g, s_rec + rec_slot(j), m);
         s_mask[j] = m;
         if (WITH_SLOT) s_slot[j] = pair_slot(slot_of, rect, g, tx, ty);
     }
@@ -453,11 +483,12 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
                                            const Splats& sp, float* __restrict__ image, float* __restrict__ t_final,
                                            uint32_t* __restrict__ n_contrib) {
     using G = TileGeom<TS>;
-    __shared__ SplatRec s_rec[kBlendBatch];
+    __shared__ SplatRec s_rec[rec_slots(kBlendBatch)];
     __shared__ typename G::Mask s_mask[kBlendBatch];
     const int tx = tile % f.TX, ty = tile / f.TX;
     const float ox = (float)(tx * TS), oy = (float)(ty * TS);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    init_null_splats(s_rec, kBlendBatch);
     FwdPixels<TS> P;
     P.init(warp, lane);
     for (uint32_t start = range.x; start < range.y; start += kBlendBatch) {
@@ -484,7 +515,7 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
 // Shared memory of the backward and fused kernels, staging BATCH splats.
 template <int TS, int BATCH = kBlendBatch>
 struct BwdSmem {
-    SplatRec rec[BATCH];
+    SplatRec rec[rec_slots(BATCH)];
     typename TileGeom<TS>::Mask mask[BATCH];
     uint32_t slot[BATCH];
     float part[kBwdChunk][2 * TileGeom<TS>::WARPS][kPart];
@@ -558,6 +589,7 @@ __device__ __forceinline__ void train_tile(const Frame& f, int tile, uint2 range
     const FloatSplats sp{splats};
     const uint32_t len = range.y - range.x;
     const int nb = (int)((len + kBlendBatch - 1) / kBlendBatch);
+    init_null_splats(sm.rec, kBlendBatch);
     BwdPixels<TS> B;
     {
         FwdPixels<TS> P;

@@ -179,12 +179,23 @@ constexpr double kOpacityLogitMin = -5.537334267018537;
 // every pair.
 constexpr float kLog2AlphaMin = -7.994353436858858f;  // log2(1/255)
 constexpr float kTwoLn2 = 1.3862943611198906f;
+constexpr float kLn2 = 0.6931471805599453f;
 // The extent threshold from L = log2(sigma): e >= log2(1/255) <=> q <= q_c
 // with q_c = 2 ln 2 (L - log2(1/255)) = 2 (ln 255 + ln sigma).
 
 __device__ __forceinline__ float splat_log2_alpha(float dx, float dy, float A, float B, float C, float L) {
     const float u = __fmaf_rn(A, dx, __fmul_rn(B, dy));
     return __fmaf_rn(dx, u, __fmaf_rn(__fmul_rn(C, dy), dy, L));
+}
+
+// The splat's axis basis from t = tan(theta / 2): e1 = (ct, st) along the
+// major axis of Sigma', e2 = (-st, ct). The pre-processing stores t, and
+// the backward blend and the pre-processing adjoint both rebuild the basis
+// here, so they use the same one to the last bit.
+__device__ __forceinline__ void axis_basis(float t, float& ct, float& st) {
+    const float r = rcp_approx(fmaf(t, t, 1.f));  // |e1| = 1 to a few ulp
+    ct = fmaf(-t, t, 1.f) * r;
+    st = 2.f * t * r;
 }
 
 

@@ -39,15 +39,16 @@ __device__ __forceinline__ float2 unpack_half2(uint32_t w) {
                        __half2float(__ushort_as_half((unsigned short)(w >> 16))));
 }
 
-// Major / minor axes of [[sxx, sxy], [sxy, syy]]: v1 = sqrt(l1) e1, v2 =
-// sqrt(l2) e2 with e2 = e1 turned by +90 degrees. e1 comes from whichever row
-// of (Sigma' - l1 I) is better conditioned; l2 = det / l1.
-__device__ __forceinline__ void ellipse_axes(float sxx, float sxy, float syy, float& v1x, float& v1y, float& v2x,
-                                             float& v2y) {
+// Major / minor axes of [[sxx, sxy], [sxy, syy]] with determinant det:
+// v1 = sqrt(l1) e1, v2 = sqrt(l2) e2 with e2 = e1 turned by +90 degrees. e1
+// comes from whichever row of (Sigma' - l1 I) is better conditioned;
+// l2 = det / l1.
+__device__ __forceinline__ void ellipse_axes(float sxx, float sxy, float syy, float det, float& v1x, float& v1y,
+                                             float& v2x, float& v2y) {
     const float m = 0.5f * (sxx + syy), h = 0.5f * (sxx - syy);
     const float d = sqrtf(fmaf(h, h, sxy * sxy));
     const float l1 = m + d;
-    const float l2 = fmaf(sxx, syy, -sxy * sxy) / l1;
+    const float l2 = det / l1;
     float ex = 1.f, ey = 0.f;
     if (d > 0.f) {
         if (h >= 0.f) {
@@ -158,7 +159,8 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
             // pack: opacity on 8 bits, ellipse as binary16 axes
             a8 = quant8(1.f / (1.f + expf(-logit)));
             float v1x, v1y, v2x, v2y;
-            ellipse_axes(sxx, sxy, syy, v1x, v1y, v2x, v2y);
+            // det(Sigma') = sxx / conic c, as project_core formed it (no cancellation)
+            ellipse_axes(sxx, sxy, syy, sxx / P.cc, v1x, v1y, v2x, v2y);
             ax = make_uint2(pack_half2(v1x, v1y), pack_half2(v2x, v2y));
             // extent, viewport test and tile rectangle of the packed splat
             float qxx, qxy, qyy, det;

@@ -92,15 +92,51 @@ struct Projection {
     float4 m4;         // projected centre as double-float (x_hi, y_hi, x_lo, y_lo)
     float ca, cb, cc;  // conic = Sigma'^{-1}
     float sigma;       // peak opacity
+    float t;           // tan(theta / 2), theta in [-pi/2, pi/2] the angle of Sigma''s major axis
     uint32_t x0, y0, x1, y1;  // tile rectangle (inclusive)
 };
+
+// t = tan(theta / 2) of the major axis of [[sxx, sxy], [sxy, syy]]: an
+// eigenvector e from whichever row of (Sigma' - l1 I) is better conditioned,
+// (d + h, sxy) or (sxy, d - h) with h = (sxx - syy) / 2, d = sqrt(h^2 +
+// sxy^2), whose norm is sqrt(2 d (d + |h|)) either way; turned to e.x >= 0,
+// t = e.y / (|e| + e.x). 0 for a circle. Any t within a few ulp will do: the
+// record stores it and every user rebuilds the basis from the stored value.
+__device__ __forceinline__ float major_axis_t(float sxx, float sxy, float syy) {
+    const float h = 0.5f * (sxx - syy);
+    const float d = sqrtf(fmaf(h, h, sxy * sxy));
+    if (!(d > 0.f)) return 0.f;
+    const float dh = d + fabsf(h);
+    float ex = h >= 0.f ? dh : sxy;
+    float ey = h >= 0.f ? sxy : dh;
+    if (ex < 0.f) {
+        ex = -ex;
+        ey = -ey;
+    }
+    return __fdividef(ey, sqrtf(2.f * d * dh) + ex);
+}
 
 // Stores the splat record of one Gaussian (zeros when it is not visible).
 __device__ __forceinline__ void store_splat(float4* __restrict__ dst, bool vis, const Projection& P, float3 c3) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     dst[0] = vis ? P.m4 : z;
     dst[1] = vis ? make_float4(P.ca, P.cb, P.cc, P.sigma) : z;
-    dst[2] = make_float4(c3.x, c3.y, c3.z, 0.f);
+    dst[2] = make_float4(c3.x, c3.y, c3.z, vis ? P.t : 0.f);
+}
+
+// det(Sigma') for Sigma' = V V^T + dilation I (rows V0, V1 of V; sxx, syy the
+// diagonal with the dilation): by Lagrange's identity det(V V^T) =
+// |V0 x V1|^2, so det(Sigma') = |V0 x V1|^2 + dilation (sxx + syy) -
+// dilation^2, with sxx + syy - dilation = |V0|^2 + |V1|^2 + dilation: a sum
+// of non-negative terms. sxx syy - sxy^2 would cancel for an elongated splat
+// (condition number 3e4 costs it ~3e-4 of relative error in float32) and
+// the conic, a common factor 1/det, would carry that error into every alpha.
+__device__ __forceinline__ float sigma2d_det(const float V0[3], const float V1[3], float sxx, float syy, float dil) {
+    const float c0 = fmaf(V0[1], V1[2], -V0[2] * V1[1]);
+    const float c1 = fmaf(V0[2], V1[0], -V0[0] * V1[2]);
+    const float c2 = fmaf(V0[0], V1[1], -V0[1] * V1[0]);
+    const float cross2 = fmaf(c0, c0, fmaf(c1, c1, c2 * c2));
+    return fmaf(dil, sxx + syy - dil, cross2);
 }
 
 // Projection of one Gaussian that passed the opacity and near-plane tests:
@@ -146,12 +182,13 @@ __device__ __forceinline__ bool project_core(const Frame& f, float x, float y, f
     sxx = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2] + f.dilation;
     sxy = V0[0] * V1[0] + V0[1] * V1[1] + V0[2] * V1[2];
     syy = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2] + f.dilation;
-    const float det = fmaf(sxx, syy, -sxy * sxy);
+    const float det = sigma2d_det(V0, V1, sxx, syy, f.dilation);
     if (!(det > 0.f)) return false;
     const float id = 1.f / det;
     P.ca = syy * id;
     P.cb = -sxy * id;
     P.cc = sxx * id;
+    P.t = major_axis_t(sxx, sxy, syy);
     return true;
 }
 
@@ -229,13 +266,24 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* 
 
 
 // Adjoint of project_splat's geometry for one view: given the summed pair
-// derivatives pr[0..4] = dL/d(centre x, y; conic a, b, c), ADDS dL/dmeans,
+// derivatives pr[0..1] = dL/d(centre x, y) and pr[2..4] = dL/d(alpha, beta,
+// gamma), the conic in the splat's axis basis (axis_basis(axis_t): q = alpha u^2 +
+// 2 beta u v + gamma v^2 with u = e1 . d, v = e2 . d), ADDS dL/dmeans,
 // dL/dlog_scales and dL/dquats into gm, gls, gq. The chain: conic =
 // Sigma'^{-1}, Sigma' = V V^T + dilation I, V = J W M (the guard-band clamp of
 // J passes no gradient), M = R(q) diag(exp(log_scale)), q normalised, and the
 // pinhole projection of the centre.
+//
+// Why the axis basis: for an elongated splat (Sigma' eigenvalues 1e4 and 0.3
+// px^2, say) the pixels far along its major axis give conic derivatives of
+// order dp u^2 ~ 1e6 dp, while dL/dSigma' = -C dL/dC C scales the along-axis
+// part by the conic's small eigenvalue squared (1e-8). In x, y coordinates
+// that part is lost under the rounding of the large entries, and the
+// gradient of the major axis's scale comes out wrong by several times its
+// size; summed and transformed in the axis basis, each part keeps its own
+// relative precision.
 __device__ __forceinline__ void splat_adjoint(const Frame& f, const float X[3], float4 q4, const float ls[3],
-                                              const float pr[9], float gm[3], float gls[3], float gq[4]) {
+                                              const float pr[9], float axis_t, float gm[3], float gls[3], float gq[4]) {
     // forward quantities
     const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
     const float qinv = rsqrtf(qn2);
@@ -273,13 +321,30 @@ __device__ __forceinline__ void splat_adjoint(const Frame& f, const float X[3], 
     const float sxy = V[0][0] * V[1][0] + V[0][1] * V[1][1] + V[0][2] * V[1][2];
     const float syy = V[1][0] * V[1][0] + V[1][1] * V[1][1] + V[1][2] * V[1][2] + f.dilation;
 
-    // conic = Sigma'^{-1}: (a, b, c) = (syy, -sxy, sxx) / D
-    const float D = fmaf(sxx, syy, -sxy * sxy), iD = 1.f / D, iD2 = iD * iD;
-    const float ga = pr[2], gb = pr[3], gc = pr[4];
-    const float gp = ga * (-syy * syy * iD2) + gb * (sxy * syy * iD2) + gc * (iD - sxx * syy * iD2);
-    const float gs = ga * (iD - syy * sxx * iD2) + gb * (sxy * sxx * iD2) + gc * (-sxx * sxx * iD2);
-    const float gr = ga * (2.f * sxy * syy * iD2) + gb * (-iD - 2.f * sxy * sxy * iD2) + gc * (2.f * sxy * sxx * iD2);
-    const float G2[2][2] = {{gp, 0.5f * gr}, {0.5f * gr, gs}};
+    // conic C = Sigma'^{-1} = [[syy, -sxy], [-sxy, sxx]] / D. In the axis
+    // basis Ce = [[alpha, beta], [beta, gamma]]: gamma = e2^T C e2 (the large
+    // eigenvalue's side), beta = e1^T C e2 (small: the basis is the axes'
+    // to rounding), alpha = (det C + beta^2) / gamma with det C = 1 / D, not
+    // e1^T C e1, which would cancel.
+    const float D = sigma2d_det(V[0], V[1], sxx, syy, f.dilation), iD = 1.f / D;
+    const float ca = syy * iD, cb = -sxy * iD, cc = sxx * iD;
+    float ct, st;
+    axis_basis(axis_t, ct, st);
+    const float ce2x = fmaf(cb, ct, -ca * st), ce2y = fmaf(cc, ct, -cb * st);  // C e2
+    const float gam = fmaf(ct, ce2y, -st * ce2x);
+    const float bet = fmaf(ct, ce2x, st * ce2y);
+    const float alp = fmaf(bet, bet, iD) / gam;
+    // dL/dSigma_e = -Ce G Ce with G = [[g00, g01], [g01, g11]] = dL/dCe
+    const float g00 = pr[2], g01 = 0.5f * pr[3], g11 = pr[4];
+    const float m00 = fmaf(g00, alp, g01 * bet), m01 = fmaf(g00, bet, g01 * gam);
+    const float m10 = fmaf(g01, alp, g11 * bet), m11 = fmaf(g01, bet, g11 * gam);
+    const float h00 = -fmaf(alp, m00, bet * m10), h01 = -fmaf(alp, m01, bet * m11);
+    const float h11 = -fmaf(bet, m01, gam * m11);
+    // back to x, y: dL/dSigma' = E H E^T with E = [e1 e2] = [[ct, -st], [st, ct]]
+    const float cs = ct * st, c2 = ct * ct, s2 = st * st;
+    const float G2xy = fmaf(cs, h00 - h11, (c2 - s2) * h01);
+    const float G2[2][2] = {{fmaf(c2, h00, fmaf(s2, h11, -2.f * cs * h01)), G2xy},
+                            {G2xy, fmaf(s2, h00, fmaf(c2, h11, 2.f * cs * h01))}};
     // Sigma' = V V^T: dV = 2 G2 V; V = Tm M: dTm = dV M^T, dM = Tm^T dV
     float dV[2][3];
 #pragma unroll

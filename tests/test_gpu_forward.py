@@ -129,8 +129,9 @@ def test_ragged_resolution_and_background():
 
 def test_culled_entries_are_written_as_zeros():
     """Every output entry is written: a culled Gaussian's splat record (centre,
-    conic, opacity, colour) and rect are zeros, and every record's padding
-    word is zero, whatever the buffers held before."""
+    conic, opacity, colour, axis word) and rect are zeros, whatever the
+    buffers held before; a visible one's axis word t = tan(theta / 2) gives
+    the major axis of the oracle's 2D covariance."""
     import torch
     from paper_2602_03207_gb300 import render
     scene, cam = S.small_forward()
@@ -152,7 +153,25 @@ def test_culled_entries_are_written_as_zeros():
     for k in ("mean2d4", "conic", "rgb", "opacity", "rect"):
         np.testing.assert_array_equal(g[k][culled], 0)
         assert np.isfinite(g[k][~culled].astype(np.float64)).all(), k
-    np.testing.assert_array_equal(r.splats[:n, 11].cpu().numpy(), 0)
+    t = r.splats[:n, 11].cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(t[culled], 0)
+    assert (np.abs(t[~culled]) <= 1.0).all()
+    # the axis (theta modulo pi) against the oracle's covariance: compare
+    # (cos 2 theta, sin 2 theta), which the eigenvector's sign leaves alone,
+    # where the eigenvalues differ enough to fix the axis
+    ref = oracle.preprocess(scene, cam)
+    cov = ref["cov2d"][~culled]
+    h, b2 = 0.5 * (cov[:, 0] - cov[:, 2]), cov[:, 1]
+    d = np.hypot(h, b2)
+    gap = d / (0.5 * (cov[:, 0] + cov[:, 2]))
+    th = 2.0 * np.arctan(t[~culled])
+    ok = gap > 1e-3
+    assert ok.sum() > 100
+    # float32 covariance entries (relative error ~1e-6) turn the axis by
+    # about that error over the relative eigenvalue gap
+    tol = 1e-5 + 4e-6 / gap[ok]
+    assert (np.abs(np.cos(2 * th) - h / d)[ok] <= tol).all()
+    assert (np.abs(np.sin(2 * th) - b2 / d)[ok] <= tol).all()
 
 
 def test_empty_and_fully_culled_scenes():
