@@ -34,10 +34,11 @@ WORKLOADS = {
 METRIC = "1080p frames/s at 1M splats"
 METRICS = {"hd": METRIC, "uhd": "2160p frames/s at 6M splats"}
 # DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernel (profiles/kernels_hd_1080p_1M.md: k_blend on the 1080p frame;
-# profiles/kernels_bwd_720p_500k.md: k_blend_bwd on the 720p training step);
-# to be reset to None whenever that kernel changes.
-KERNEL_TRAFFIC = {("k_blend", 16): 51_982_592 + 11_175_424, ("k_blend_bwd", 16): 49_810_432 + 1_607_168}
+# kernel (k_blend on the 1080p frame; k_blend_bwd and k_train on the 720p
+# training step; the captures' summaries are kept under profiles/); to be
+# reset to None whenever that kernel changes.
+KERNEL_TRAFFIC = {("k_blend", 16): 51_965_696 + 11_462_656, ("k_blend_bwd", 16): 49_817_344 + 1_578_496,
+                  ("k_train", 16): 42_855_680 + 4_549_632}
 STAGES = ("preprocess", "cull", "sort", "rasterize")
 
 
@@ -643,7 +644,7 @@ def summarize(args, r, scene, cams, stage_ms, elapsed, value, frames, e2e, clock
     # (offsets, quadratic form, scale by opacity) + 8 to composite for the
     # pi/4 of them inside the ellipse the box bounds.
     evals = tot["evals0"] * (keys / max(tot["keys0"], 1))
-    flops = evals * (11.0 + 8.0 * math.pi / 4.0)
+    flops = fwd_flops(evals)
     ms = stage_ms["rasterize"]
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     peak_tflops = sm_count * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
@@ -703,7 +704,7 @@ def extra_workloads(args, dev, out):
     import torch
     torch.cuda.empty_cache()
     if not args.no_train:
-        out["train"] = train_block(args, dev)
+        out["train"] = train_block(args, dev, min_timed_s=min(1.0, args.min_timed_s))
         torch.cuda.empty_cache()
     if not args.no_batch:
         out["batch"] = batch_block(args, dev)
@@ -755,7 +756,13 @@ def cpu_baseline(args, frames=2):
 
 BWD_FLOPS_TEST = 11.0      # per evaluation: offsets, quadratic form, the 1/255 test
 BWD_FLOPS_COMPOSITE = 43.0  # per composited evaluation: T before the pair, colour,
-#                             alpha and conic partials (see DESIGN: backward roofline)
+#                             alpha, conic and centre partials
+
+
+def fwd_flops(evals):
+    """Algorithmic FP32 work of the forward blend over `evals` evaluations:
+    11 FLOPs to the 1/255 test each, 8 more for the pi/4 that composite."""
+    return evals * (11.0 + 8.0 * math.pi / 4.0)
 
 
 def bwd_flops(evals):
@@ -780,8 +787,11 @@ def _events(k):
 def train_block(args, dev, min_timed_s=1.0, stage_steps=100):
     """Single-view training steps: forward + L2 residual + backward of the
     500,000-Gaussian 1280x720 scene against a U[0,1) target (the gradient
-    parity workload). Timed regions of K steps as the frame metric, plus a
-    per-stage split from a separate run with an event between stages."""
+    parity workload). Timed regions of K steps as the frame metric, for the
+    separate calls (ws_rasterize, ws_image_residual, ws_rasterize_backward)
+    and for the fused pass (ws_render_train_l2), which gives the same bits;
+    the faster is the value. Plus a per-stage split of the separate calls
+    from a run with an event between stages."""
     import torch
     from paper_2602_03207_gb300 import capi, render, synthetic as S
     scene_np, cam, target = S.grad_scene()
@@ -802,15 +812,22 @@ def train_block(args, dev, min_timed_s=1.0, stage_steps=100):
         capi.ws_image_residual(tgt.numel(), r.image, tgt, d)
         r.backward(scene, cam, d)
 
+    def step_fused():  # pre-processing, compaction, sort, then the fused pass
+        r.train_step_l2(scene, cam, tgt)
+
     for _ in range(max(args.warmup, 3)):
         step()
+        step_fused()
     torch.cuda.synchronize()
     r.check_status()
     steps = max(3, args.steps)
+    timed = {}
     with ClockSampler(dev.index) as clk:
-        region_s, t_region, regions = timed_regions(lambda o, k: [step() for _ in range(k)], steps, stream,
-                                                    min_timed_s)
+        for name, fn in (("separate", step), ("fused", step_fused)):
+            timed[name] = timed_regions(lambda o, k: [fn() for _ in range(k)], steps, stream, min_timed_s)
     r.check_status()
+    path = min(timed, key=lambda nm: timed[nm][1])
+    region_s, t_region, regions = timed[path]
     t = t_region / steps
     # per-stage split
     names = ("preprocess", "cull", "sort", "rasterize", "residual", "backward")
@@ -831,6 +848,17 @@ def train_block(args, dev, min_timed_s=1.0, stage_steps=100):
         e[6].record(stream)
     torch.cuda.synchronize()
     stage_ms = {nm: sum(e[j].elapsed_time(e[j + 1]) for e in ev) / stage_steps for j, nm in enumerate(names)}
+    # the fused path's split: the same three stages, then ws_render_train_l2
+    fev = [_events(2) for _ in range(stage_steps)]
+    for e in fev:
+        r.preprocess(scene, ccam)
+        r.cull(ccam)
+        r.sort()
+        e[0].record(stream)
+        r.train_pass_l2(scene, cam, tgt)
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    fused_ms = sum(e[0].elapsed_time(e[1]) for e in fev) / stage_steps
     kk = r.key_count()
     f = {"mean2d": (r.mean2d[:n, :2].double() + r.mean2d[:n, 2:].double()).cpu().numpy(),
          "conic": r.conic[:n].cpu().numpy(), "opacity": r.opacity[:n].cpu().numpy(),
@@ -838,20 +866,33 @@ def train_block(args, dev, min_timed_s=1.0, stage_steps=100):
          "sorted_vals": r.sorted_vals[:kk].cpu().numpy().view(np.uint32)}
     evals = blend_work(f, r.width, r.height, r.tile)
     peak = fp32_peak_tflops()
-    ach = bwd_flops(evals) / (stage_ms["backward"] * 1e-3) / 1e12
+    if path == "fused":
+        ach = (fwd_flops(evals) + bwd_flops(evals)) / (fused_ms * 1e-3) / 1e12
+        roof = {"kernel": f"k_train<{r.tile}> (timed span: ws_render_train_l2)", "bound": "alu",
+                "alg_evals": int(evals), "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": KERNEL_TRAFFIC.get(("k_train", r.tile)),
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        ach = bwd_flops(evals) / (stage_ms["backward"] * 1e-3) / 1e12
+        roof = {"kernel": f"k_blend_bwd<{r.tile}> (timed span: ws_rasterize_backward)", "bound": "alu",
+                "alg_evals": int(evals), "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": KERNEL_TRAFFIC.get(("k_blend_bwd", r.tile)),
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"}
     return {"metric": "720p fwd+bwd steps/s at 500k splats", "value": round(1.0 / t, 2), "unit": "steps/s",
             "steps": steps, "ms_per_step": round(t * 1e3, 4),
             "timing": {"regions": regions, "steps_per_region": steps, "statistic": "median region",
                        "region_ms": {"min": round(min(region_s) * 1e3, 3),
                                      "max": round(max(region_s) * 1e3, 3)}},
             "config": {"workload": "500,000 Gaussians, 1280x720, SH3, forward + L2 residual + backward",
-                       "tile": args.tile, "digit_bits": args.digit_bits, "pairs": kk},
+                       "tile": args.tile, "digit_bits": args.digit_bits, "pairs": kk,
+                       "path": {"separate": "ws_rasterize + ws_image_residual + ws_rasterize_backward",
+                                "fused": "ws_render_train_l2"}[path]},
+            "step_variants": {nm: {"ms_per_step": round(v[1] / steps * 1e3, 4), "steps_s": round(steps / v[1], 2)}
+                              for nm, v in timed.items()},
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-            "roofline": {"kernel": f"k_blend_bwd<{r.tile}> (timed span: ws_rasterize_backward)", "bound": "alu",
-                         "alg_evals": int(evals), "achieved": round(ach, 3), "peak": round(peak, 2),
-                         "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-                         "traffic": KERNEL_TRAFFIC.get(("k_blend_bwd", r.tile)),
-                         "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"},
+            "stages_note": "separate calls, an event between stages; the fused pass alone (ws_render_train_l2 "
+                           "after the sort): " + f"{fused_ms:.4f} ms",
+            "roofline": roof,
             "clocks": clk.summary()}
 
 
@@ -1032,7 +1073,7 @@ def run_train(args):
     import torch
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    out = train_block(args, dev)
+    out = train_block(args, dev, min_timed_s=min(1.0, args.min_timed_s))
     out.update({"n_gpus": 1, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded cluster scene, U[0,1) target)"})
     return out

@@ -244,6 +244,12 @@ class Renderer:
         self.preprocess(scene, cam, stream)
         self.cull(cam, stream)
         self.sort(stream)
+        return self.train_pass_l2(scene, cam_dict, target, stream)
+
+    def train_pass_l2(self, scene, cam_dict, target, stream=None):
+        """The fused pass of train_step_l2 alone (ws_render_train_l2), on the
+        pairs this renderer has sorted for the same scene and camera."""
+        cam = capi.camera(cam_dict)
         g = self._grads()
         capi.ws_render_train_l2(self.n, scene["means"], scene["log_scales"], scene["quats"], scene["sh"], cam,
                                 self.raster_cfg, self.num_keys, self.sorted_keys, self.sorted_vals, self.splats, self.rect,
