@@ -233,6 +233,36 @@ ws_status ws_sort_tiles(const uint32_t *num_keys, int64_t key_capacity, int32_t 
                         void *workspace, uint32_t *ranges, int64_t ntiles, int32_t *result_in_alt,
                         void *stream);
 
+/* ws_cull followed by ws_sort_tiles of the frame's keys (end_bit the
+ * smallest with 2^(end_bit - 31) >= the tile count, at least 32), with the
+ * compaction fused into the sort's first partition pass: instead of writing
+ * the pairs in slot order, the compaction writes each one where that pass
+ * would put it (the stable partition of the slot-ordered pairs by the low D
+ * bits of the tile id, D the first digit of the segmented sort: 7 at 1080p
+ * with 16-pixel tiles and 9-bit digits). Per chunk of Gaussians it counts
+ * the pairs of each digit from the rectangles, scans each digit's counts
+ * over the chunks, and scatters every pair to base_d + (pairs of digit d in
+ * earlier chunks) + (its rank among the chunk's pairs of digit d in slot
+ * order): no block waits for another, no global atomics. The results --
+ * offsets, num_keys, the sorted keys and vals, ranges, *result_in_alt and
+ * the status word -- are bit-identical to those of ws_cull and
+ * ws_sort_tiles; pass WS_CFG_RANGES_GIVEN to the following rasterisation.
+ * When the frame has more pairs than key_capacity the compaction writes the
+ * first key_capacity slots in slot order instead (as ws_cull) and
+ * WS_FLAG_CAPACITY is raised; the sorted list is then not meaningful, but
+ * every entry below num_keys holds a valid pair. The workspace must come
+ * from ws_workspace_bytes with the same n. Returns WS_ERR_UNSUPPORTED when
+ * ws_sort_tiles would, or when the first digit is wider than 8 bits (take
+ * ws_cull and ws_sort_tiles then). Measured on GB300 at 1080p / 1M: no
+ * faster than the two calls (the fused emission costs what the emission and
+ * the first pass's scatter cost together, and counting the digits from the
+ * rectangles what the first pass's histograms cost). */
+ws_status ws_cull_sort_tiles(int64_t n, const uint32_t *tiles_touched, const uint16_t *rect, const float *depth,
+                             const ws_camera *cam, const ws_config *cfg, uint32_t *offsets, uint64_t *keys,
+                             uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t key_capacity,
+                             uint32_t *num_keys, uint32_t *ranges, void *workspace, int32_t *result_in_alt,
+                             void *stream);
+
 /* Test hook of the look-back variant: tile `stalled_tile` of the first pass
  * never publishes its counts, so every later tile's bounded wait runs out.
  * Lets a test check that a stalled predecessor ends in WS_FLAG_TIMEOUT and a

@@ -28,14 +28,14 @@ WS_CFG_PERSISTENT = 32
 WS_CFG_RANGES_GIVEN = 64
 WS_CFG_BOX_MASKS = 128
 WS_ABI_VERSION = 2
-WS_SPLAT_FLOATS = 12  # floats per splat record: centre hi/lo (4), conic (3), sigma, colour (3), 0
+WS_SPLAT_FLOATS = 12  # floats per splat record: centre hi/lo (4), conic (3), sigma, colour (3), axis word
 
 EXPORTS = ("ws_abi_version", "ws_status_string", "ws_workspace_bytes", "ws_preprocess", "ws_cull",
            "ws_sort", "ws_sort_noalloc", "ws_sort_noalloc_max_keys", "ws_rasterize",
            "ws_rasterize_backward", "ws_read_status", "ws_batch_max_views", "ws_batch_workspace_bytes",
            "ws_preprocess_batch", "ws_cull_batch", "ws_rasterize_batch", "ws_rasterize_backward_batch",
            "ws_image_residual", "ws_sort_test_stalled_tile", "ws_render_train_l2", "ws_render_train_l2_batch",
-           "ws_sort_tiles", "ws_render_frame_host")
+           "ws_sort_tiles", "ws_render_frame_host", "ws_cull_sort_tiles")
 
 
 class WsError(RuntimeError):
@@ -112,6 +112,9 @@ def lib():
             L.ws_sort_test_stalled_tile.restype = I32
             L.ws_sort_tiles.argtypes = [P, I64, I32, P, P, P, P, cfg_p, P, P, I64, C.POINTER(I32), P]
             L.ws_sort_tiles.restype = I32
+            L.ws_cull_sort_tiles.argtypes = [I64, P, P, P, cam_p, cfg_p, P, P, P, P, P, I64, P, P, P,
+                                             C.POINTER(I32), P]
+            L.ws_cull_sort_tiles.restype = I32
             L.ws_render_frame_host.argtypes = [I64, P, P, P, P, P, cam_p, cfg_p, C.POINTER(FrameBuffers), P, P]
             L.ws_render_frame_host.restype = I32
             L.ws_sort_noalloc.argtypes = [P, I64, I32, I32, P, P, P, P, I32, C.POINTER(I32), P]
@@ -199,6 +202,18 @@ def ws_sort_tiles(num_keys, key_capacity, end_bit, keys, vals, keys_alt, vals_al
     _check("ws_sort_tiles", lib().ws_sort_tiles(
         _ptr(num_keys), int(key_capacity), int(end_bit), _ptr(keys), _ptr(vals), _ptr(keys_alt), _ptr(vals_alt),
         C.byref(cfg), _ptr(workspace), _ptr(ranges), int(ntiles), C.byref(in_alt), _stream(stream)))
+    return bool(in_alt.value)
+
+
+def ws_cull_sort_tiles(n, tiles_touched, rect, depth, cam, cfg, offsets, keys, vals, keys_alt, vals_alt,
+                       key_capacity, num_keys, ranges, workspace, stream=None) -> bool:
+    """ws_cull and ws_sort_tiles with the compaction fused into the sort's
+    first partition pass; True when the sorted pairs are in the _alt buffers."""
+    in_alt = C.c_int32(0)
+    _check("ws_cull_sort_tiles", lib().ws_cull_sort_tiles(
+        int(n), _ptr(tiles_touched), _ptr(rect), _ptr(depth), C.byref(cam), C.byref(cfg), _ptr(offsets),
+        _ptr(keys), _ptr(vals), _ptr(keys_alt), _ptr(vals_alt), int(key_capacity), _ptr(num_keys), _ptr(ranges),
+        _ptr(workspace), C.byref(in_alt), _stream(stream)))
     return bool(in_alt.value)
 
 

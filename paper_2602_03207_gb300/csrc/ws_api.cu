@@ -131,7 +131,8 @@ const char* ws_status_string(ws_status s) {
 size_t ws_workspace_bytes(int64_t n, int64_t key_capacity, const ws_camera* cam, const ws_config* cfg) {
     if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 31)) return 0;
     if (!valid_camera(cam) || !valid_config(cfg) || !ws::sort_digit_supported(cfg->digit_bits)) return 0;
-    return layout(n, key_capacity).total;
+    // one view: the layout, then the fused compaction's digit counts
+    return layout(n, key_capacity).total + align_up(ws::cull_partition_scratch_bytes(n));
 }
 
 ws_status ws_preprocess(int64_t n, const float* means, const float* log_scales, const float* quats,
@@ -174,6 +175,51 @@ ws_status ws_cull(int64_t n, const uint32_t* tiles_touched, const uint16_t* rect
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return cuda_status(ws::launch_cull(n, tiles_touched, rect, depth, f, offsets, keys, vals,
                                        key_capacity, num_keys, status, ws_base + L.cull, s));
+}
+
+ws_status ws_cull_sort_tiles(int64_t n, const uint32_t* tiles_touched, const uint16_t* rect, const float* depth,
+                             const ws_camera* cam, const ws_config* cfg, uint32_t* offsets, uint64_t* keys,
+                             uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t key_capacity,
+                             uint32_t* num_keys, uint32_t* ranges, void* workspace, int32_t* result_in_alt,
+                             void* stream) {
+    if (n < 0 || n >= (int64_t(1) << 32) || key_capacity < 0 || key_capacity >= (int64_t(1) << 31) ||
+        !result_in_alt)
+        return WS_ERR_INVALID_ARG;
+    if (!valid_camera(cam) || !valid_config(cfg) || !ws::sort_digit_supported(cfg->digit_bits))
+        return WS_ERR_INVALID_ARG;
+    const void* ptrs[] = {offsets, num_keys, workspace, ranges};
+    for (const void* p : ptrs)
+        if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    if (n > 0) {
+        const void* in[] = {tiles_touched, rect, depth};
+        for (const void* p : in)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    if (key_capacity > 0) {
+        const void* kp[] = {keys, vals, keys_alt, vals_alt};
+        for (const void* p : kp)
+            if (!p || !aligned16(p)) return WS_ERR_INVALID_ARG;
+    }
+    const Frame f = make_frame(cam, cfg);
+    const int64_t tiles = (int64_t)f.TX * f.TY;
+    int end_bit = 31;
+    while ((int64_t(1) << (end_bit - 31)) < tiles) ++end_bit;
+    if (end_bit == 31) end_bit = 32;
+    const int digit = ws::sort_segmented_first_digit(end_bit, cfg->digit_bits);
+    if (!ws::sort_segmented_supported(key_capacity, 0, end_bit) || !ws::cull_partition_supported(digit))
+        return WS_ERR_UNSUPPORTED;
+    const Layout L = layout(n, key_capacity);
+    char* ws_base = static_cast<char*>(workspace);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws_base + L.status);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = ws::launch_cull_partition(n, tiles_touched, rect, depth, f, digit, offsets, keys, vals,
+                                              key_capacity, num_keys, status, ws_base + L.cull, ws_base + L.total, s);
+    if (e != cudaSuccess) return WS_ERR_CUDA;
+    int in_alt = 0;
+    e = ws::launch_sort_segmented(num_keys, key_capacity, 0, end_bit, cfg->digit_bits, keys, vals, keys_alt,
+                                  vals_alt, ws_base + L.sort, &in_alt, s, ranges, (uint32_t)tiles, true);
+    *result_in_alt = in_alt;
+    return cuda_status(e);
 }
 
 ws_status ws_sort(const uint32_t* num_keys, int64_t key_capacity, int32_t begin_bit, int32_t end_bit,
@@ -320,13 +366,15 @@ ws_status ws_render_frame_host(int64_t n, const float* h_means, const float* h_l
     ws_status st = ws_preprocess(n, b->means, b->log_scales, b->quats, b->opacity_logits, b->sh, cam, cfg,
                                  b->splats, b->depth, b->rect, b->tiles_touched, stream);
     if (st != WS_OK) return st;
-    st = ws_cull(n, b->tiles_touched, b->rect, b->depth, cam, cfg, b->offsets, b->keys, b->vals, b->key_capacity,
-                 b->num_keys, b->workspace, stream);
-    if (st != WS_OK) return st;
     const int64_t tiles = (int64_t)((cam->width + cfg->tile - 1) / cfg->tile) * ((cam->height + cfg->tile - 1) / cfg->tile);
     int end_bit = 31;
     while ((int64_t(1) << (end_bit - 31)) < tiles) ++end_bit;
     if (end_bit == 31) end_bit = 32;
+    // ws_cull then the sort (ws_cull_sort_tiles gives the same results and,
+    // on GB300, no gain over the two calls)
+    st = ws_cull(n, b->tiles_touched, b->rect, b->depth, cam, cfg, b->offsets, b->keys, b->vals, b->key_capacity,
+                 b->num_keys, b->workspace, stream);
+    if (st != WS_OK) return st;
     ws_config rc = *cfg;
     int32_t in_alt = 0;
     st = WS_ERR_UNSUPPORTED;

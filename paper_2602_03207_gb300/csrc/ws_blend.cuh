@@ -231,6 +231,7 @@ struct FwdPixels {
                 const int steps = max(__popc(ba), __popc(bb));
                 const SplatRec* grp = s_rec + base + (base >> 5);  // grp[0]: the null splat
                 int lastk = 0;
+#pragma unroll 4
                 for (int it = 0; it < steps; ++it) {
                     const int q = __ffs(bits);  // 0 once this half has no visit left
                     bits &= bits - 1u;

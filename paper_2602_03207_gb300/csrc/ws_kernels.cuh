@@ -21,6 +21,16 @@ cudaError_t launch_cull(int64_t n, const uint32_t* tiles_touched, const uint16_t
                         uint32_t* vals, int64_t key_capacity, uint32_t* num_keys,
                         uint32_t* status, void* scratch, cudaStream_t stream);
 
+// ws_cull fused with the first partition pass of the segmented tile sort:
+// the keys come out stably partitioned by the low `digit_bits` bits of the
+// tile id (one view; digit_bits 4..8, cull_partition_supported).
+bool cull_partition_supported(int digit_bits);
+size_t cull_partition_scratch_bytes(int64_t n);
+cudaError_t launch_cull_partition(int64_t n, const uint32_t* tiles_touched, const uint16_t* rect, const float* depth,
+                                  const Frame& f, int digit_bits, uint32_t* offsets, uint64_t* keys, uint32_t* vals,
+                                  int64_t key_capacity, uint32_t* num_keys, uint32_t* status, void* scratch,
+                                  void* part_scratch, cudaStream_t stream);
+
 cudaError_t launch_cull_batch(int64_t n, const ViewGrid& grid, const uint32_t* tiles_touched,
                               const uint16_t* rect, const float* depth, uint32_t* offsets, uint64_t* keys,
                               uint32_t* vals, int64_t key_capacity, uint32_t* num_keys, uint32_t* status,
@@ -39,10 +49,13 @@ bool sort_segmented_supported(int64_t key_capacity, int begin_bit, int end_bit);
 size_t sort_segmented_scratch_bytes(int64_t key_capacity);
 // ranges (optional, ntiles entries of [start, end)): each segment's bounds
 // in the sorted output, for the segments below ntiles.
+// first_pass_done: the keys are already stably partitioned by the first
+// digit, sort_segmented_first_digit bits wide (launch_cull_partition).
+int sort_segmented_first_digit(int end_bit, int digit_bits);
 cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,
                                   int digit_bits, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
                                   uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream,
-                                  uint32_t* ranges = nullptr, uint32_t ntiles = 0);
+                                  uint32_t* ranges = nullptr, uint32_t ntiles = 0, bool first_pass_done = false);
 bool sort_lookback_supported(int digit_bits, int begin_bit, int end_bit);
 size_t sort_lookback_scratch_bytes(int64_t key_capacity);
 cudaError_t launch_sort_lookback(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,

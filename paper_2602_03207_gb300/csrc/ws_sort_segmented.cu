@@ -500,21 +500,33 @@ bool sort_segmented_supported(int64_t key_capacity, int begin_bit, int end_bit) 
     return nseg + 1 <= seg_starts_words(key_capacity);
 }
 
-cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,
-                                  int digit_bits, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
-                                  uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream,
-                                  uint32_t* ranges, uint32_t ntiles) {
+int sort_segmented_first_digit(int end_bit, int digit_bits) {
     // Partition by the segment bits: as few passes as digits of at most
     // digit_bits bits allow, their width split evenly (13 segment bits at
-    // digit_bits 8 or 9: 7 + 6).
+    // digit_bits 8 or 9: 7 + 6); 4 bits at least.
     const int seg_bits = end_bit - kSplitBit;
     const int max_digit = digit_bits < 4 ? 4 : (digit_bits > 11 ? 11 : digit_bits);
     const int passes = (seg_bits + max_digit - 1) / max_digit;
     const int digit = (seg_bits + passes - 1) / passes;
+    return digit < 4 ? 4 : digit;
+}
+
+cudaError_t launch_sort_segmented(const uint32_t* num_keys, int64_t key_capacity, int begin_bit, int end_bit,
+                                  int digit_bits, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                                  uint32_t* vals_alt, void* scratch, int* in_alt, cudaStream_t stream,
+                                  uint32_t* ranges, uint32_t ntiles, bool first_pass_done) {
+    const int seg_bits = end_bit - kSplitBit;
+    const int digit = sort_segmented_first_digit(end_bit, digit_bits);
+    // With first_pass_done the keys already stand stably partitioned by the
+    // first digit (the fused compaction): the passes start at the second.
+    const int part_begin = first_pass_done ? kSplitBit + digit : kSplitBit;
     int part_alt = 0;
-    cudaError_t e = launch_sort(num_keys, key_capacity, kSplitBit, end_bit, digit < 4 ? 4 : digit, keys, vals,
-                                keys_alt, vals_alt, scratch, &part_alt, stream);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (part_begin < end_bit) {
+        e = launch_sort(num_keys, key_capacity, part_begin, end_bit, digit, keys, vals, keys_alt, vals_alt, scratch,
+                        &part_alt, stream);
+        if (e != cudaSuccess) return e;
+    }
     uint64_t* pk = part_alt ? keys_alt : keys;
     uint32_t* pv = part_alt ? vals_alt : vals;
     uint64_t* ok = part_alt ? keys : keys_alt;
