@@ -10,7 +10,7 @@ from paper_2602_03207_gb300 import synthetic as S
 pytestmark = pytest.mark.gpu
 
 
-def _frames(scene_np, cam, tile=16, digit_bits=9, key_capacity=None):
+def _frames(scene_np, cam, tile=16, digit_bits=9, key_capacity=None, flags=0):
     import torch
     from paper_2602_03207_gb300 import capi, render
     dev = render.scene_to_device(scene_np)
@@ -19,7 +19,7 @@ def _frames(scene_np, cam, tile=16, digit_bits=9, key_capacity=None):
     out = []
     for fused in (False, True):
         r = render.Renderer(n, cam["width"], cam["height"], tile=tile, digit_bits=digit_bits,
-                            key_capacity=key_capacity)
+                            key_capacity=key_capacity, flags=flags)
         r.preprocess(dev, c)
         if fused:
             r.cull_sort(c)
@@ -60,6 +60,26 @@ def test_fused_cull_sort_equals_separate_calls(case):
         kw = {"digit_bits": int(case[5:]), "key_capacity": 40 * len(scene["means"])}
     a, b = _frames(scene, cam, **kw)
     assert a["num_keys"][0] > 0
+    _same(a, b)
+
+
+def test_fused_cull_sort_rows_wider_than_the_digit_range():
+    """Large splats: at 1280x720 (80-tile rows, 6-bit first digit) 719 of
+    2,000 rectangles have rows wider than the 64 digits, so a row adds a full
+    turn of the digits plus a run that may wrap; at 256x256 with 4-bit digits
+    496 have 16-tile rows, exactly one turn. Also with the culling switched
+    off (rectangles clamped into the grid)."""
+    from paper_2602_03207_gb300 import capi
+    scene = S.uniform_scene(2000, seed=5, log_scale_mean=-1.0, log_scale_std=0.4)
+    cam = S.look_at_camera((2.4, -0.8, 0.7), (0.0, 0.0, 0.0), 1280, 720)
+    for flags in (0, capi.WS_CFG_NO_AABB_CULL | capi.WS_CFG_NO_OPACITY_CULL):
+        a, b = _frames(scene, cam, key_capacity=8_000_000, flags=flags)
+        assert not (a["status"] & capi.WS_FLAG_CAPACITY)
+        _same(a, b)
+    _, cam = S.small_forward()
+    scene = S.uniform_scene(3000, seed=5, log_scale_mean=-1.0, log_scale_std=0.4)
+    a, b = _frames(scene, cam, digit_bits=4, key_capacity=600_000)
+    assert not (a["status"] & capi.WS_FLAG_CAPACITY)
     _same(a, b)
 
 
