@@ -461,14 +461,16 @@ def run_ours(args):
     r = render.Renderer(n, W, H, tile=args.tile, digit_bits=args.digit_bits, key_capacity=cap, device=dev)
     stream = torch.cuda.current_stream(dev)
     passes = math.ceil(r.end_bit / args.digit_bits)
-    # preprocess, cull (3), sort (segmented: 3 per partition pass + bounds +
-    # local), raster (tile ranges + blend)
-    launches_per_frame = 1 + 3 + seg_sort_launches(r.end_bit) + 2
 
     # warm-up
     for i in range(args.warmup):
         r.forward(scene, cams[rank_pose(rank, i)])
     r.check_status()
+    # preprocess 1, cull 3, segmented sort (3 per partition pass + bounds +
+    # local), rasterize: the blend, plus the tile-range scan unless the sort
+    # wrote the ranges (ws_sort_tiles)
+    ranges_given = bool(r.raster_cfg.flags & capi.WS_CFG_RANGES_GIVEN)
+    launches_per_frame = 1 + 3 + seg_sort_launches(r.end_bit) + (1 if ranges_given else 2)
 
     ccams = [capi.camera(c) for c in cams]
 
