@@ -92,7 +92,7 @@ k_preprocess_batch(int64_t n, const float* __restrict__ means, const float* __re
 }
 
 template <int TS>
-__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS, blend_min_blocks<TS>())
+__global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>())
 k_blend_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, int64_t n,
               const float4* __restrict__ splats, const FrameTable ft,
               float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
@@ -291,7 +291,7 @@ cudaError_t launch_rasterize_batch(const uint32_t* num_keys, const uint64_t* key
             return launch_pdl(k_blend_batch<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, s4, ft, image,
                               t_final, n_contrib);
         case 32:
-            return launch_pdl(k_blend_batch<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, n, s4, ft, image,
+            return launch_pdl(k_blend_batch<32>, dim3(ntiles), dim3(1024), 0, stream, r2, vals, n, s4, ft, image,
                               t_final, n_contrib);
         default:
             return cudaErrorInvalidValue;

@@ -14,9 +14,10 @@ constexpr int kBwdChunk = 64;     // splats whose partials the backward holds at
 constexpr int kPart = 9;          // dmean x, y; dconic a, b, c; sigma dsigma; drgb r, g, b
 
 // Blocks per SM that the forward blends are compiled for (their register
-// budget): 64 threads x 16, 256 x 8 and 256 x 4 for 8, 16 and 32 pixel tiles.
+// budget): 64 threads x 16, 256 x 8 and 1024 x 2 for 8, 16 and 32 pixel
+// tiles (one thread per pixel).
 template <int TS>
-constexpr int blend_min_blocks() { return TS == 8 ? 16 : (TS == 16 ? 8 : 4); }
+constexpr int blend_min_blocks() { return TS == 8 ? 16 : (TS == 16 ? 8 : 2); }
 
 // Shared-memory record of one staged splat (48 bytes):
 //   geo  = tile-relative centre x, y; conic premultiplied A = -log2(e) a / 2,
@@ -68,13 +69,15 @@ struct FloatSplats {
     }
 };
 
-// Geometry of a TS x TS tile: THREADS threads, one per pixel of one 8x4
-// region per warp (PPT regions per warp when the tile has more pixels than
-// threads); each region is two 4x4 sub-blocks, one per half-warp. A splat's
-// mask has one bit per sub-block (row-major, SPR per row).
-template <int TS>
+// Geometry of a TS x TS tile: TH threads, one per pixel of one 8x4 region per
+// warp (PPT regions per warp when the tile has more pixels than threads);
+// each region is two 4x4 sub-blocks, one per half-warp. A splat's mask has
+// one bit per sub-block (row-major, SPR per row). The backward and the fused
+// training pass take at most 256 threads (their per-half-warp partial
+// buffers grow with the warps); the forward blend takes one thread per pixel.
+template <int TS, int TH = (TS * TS >= 256 ? 256 : TS * TS)>
 struct TileGeom {
-    static constexpr int THREADS = TS * TS >= 256 ? 256 : TS * TS;
+    static constexpr int THREADS = TH;
     static constexpr int WARPS = THREADS / 32;
     static constexpr int PPT = TS * TS / THREADS;
     static constexpr int RPR = TS / 8;  // regions per row
@@ -191,9 +194,9 @@ __device__ __forceinline__ void stage_splat(const Frame& f, float ox, float oy, 
 }
 
 // Forward state of a thread's pixels: front to back, C += c a T, T -= a T.
-template <int TS>
+template <int TS, int TH = TileGeom<TS>::THREADS>
 struct FwdPixels {
-    using G = TileGeom<TS>;
+    using G = TileGeom<TS, TH>;
     float px[G::PPT], py[G::PPT], T[G::PPT], C0[G::PPT], C1[G::PPT], C2[G::PPT];
     uint32_t last[G::PPT];
     int sb[G::PPT];
@@ -458,12 +461,12 @@ __device__ __forceinline__ void zero_records(uint2 range, uint32_t from, const u
 // and (WITH_SLOT) each pair's emission slot. The stagings of the backward
 // and of the fused training pass (WITH_SLOT) build the ellipse's sub-block
 // masks, the forward's the bounding box's.
-template <int TS, bool WITH_SLOT, typename Splats, typename SlotBase>
+template <int TS, bool WITH_SLOT, typename Splats, typename SlotBase, int TH = TileGeom<TS>::THREADS>
 __device__ __forceinline__ void stage_batch(const Frame& f, float ox, float oy, int tx, int ty, uint32_t start,
                                             int cnt, const uint32_t* __restrict__ vals, const Splats& sp,
                                             const uint2* __restrict__ rect, SlotBase slot_of, SplatRec* s_rec,
                                             typename TileGeom<TS>::Mask* s_mask, uint32_t* s_slot) {
-    for (int j = threadIdx.x; j < cnt; j += TileGeom<TS>::THREADS) {
+    for (int j = threadIdx.x; j < cnt; j += TH) {
         const uint32_t g = __ldg(vals + start + j);
         typename TileGeom<TS>::Mask m;
         stage_splat<TS, WITH_SLOT>(f, ox, oy, sp, g, s_rec + rec_slot(j), m);
@@ -476,26 +479,29 @@ struct NoSlot {
     __device__ __forceinline__ uint32_t operator()(uint32_t) const { return 0u; }
 };
 
-// Forward of one tile: stages the list 256 splats at a time and composites
-// each batch (FwdPixels::batch), then writes image = C + T bg, the final
-// transmittance and the 1-based list position of the last composited splat.
+// Forward of one tile, one thread per pixel (TS * TS threads): stages the
+// list 256 splats at a time and composites each batch (FwdPixels::batch),
+// then writes image = C + T bg, the final transmittance and the 1-based list
+// position of the last composited splat.
 template <int TS, typename Splats>
 __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range, const uint32_t* __restrict__ vals,
                                            const Splats& sp, float* __restrict__ image, float* __restrict__ t_final,
                                            uint32_t* __restrict__ n_contrib) {
-    using G = TileGeom<TS>;
+    constexpr int TH = TS * TS;
+    using G = TileGeom<TS, TH>;
     __shared__ SplatRec s_rec[rec_slots(kBlendBatch)];
     __shared__ typename G::Mask s_mask[kBlendBatch];
     const int tx = tile % f.TX, ty = tile / f.TX;
     const float ox = (float)(tx * TS), oy = (float)(ty * TS);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     init_null_splats(s_rec, kBlendBatch);
-    FwdPixels<TS> P;
+    FwdPixels<TS, TH> P;
     P.init(warp, lane);
     for (uint32_t start = range.x; start < range.y; start += kBlendBatch) {
         const int cnt = (int)min((uint32_t)kBlendBatch, range.y - start);
         __syncthreads();
-        stage_batch<TS, false>(f, ox, oy, tx, ty, start, cnt, vals, sp, nullptr, NoSlot{}, s_rec, s_mask, nullptr);
+        stage_batch<TS, false, Splats, NoSlot, TH>(f, ox, oy, tx, ty, start, cnt, vals, sp, nullptr, NoSlot{}, s_rec,
+                                                   s_mask, nullptr);
         __syncthreads();
         P.batch(s_rec, s_mask, cnt, start + 1 - range.x, lane);
     }

@@ -206,7 +206,7 @@ k_preprocess_packed(int64_t n, const float* __restrict__ means, const float* __r
 }
 
 template <int TS>
-__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS, blend_min_blocks<TS>())
+__global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>())
 k_blend_packed(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                const float2* __restrict__ mean2d, const uint2* __restrict__ axes,
                const uint32_t* __restrict__ rgba, const Frame f, float* __restrict__ image,
@@ -249,7 +249,7 @@ cudaError_t launch_rasterize_packed(const uint32_t* num_keys, const uint64_t* ke
             return launch_pdl(k_blend_packed<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, m2, a2, rgba, f,
                               image, t_final, n_contrib);
         case 32:
-            return launch_pdl(k_blend_packed<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, m2, a2, rgba, f,
+            return launch_pdl(k_blend_packed<32>, dim3(ntiles), dim3(1024), 0, stream, r2, vals, m2, a2, rgba, f,
                               image, t_final, n_contrib);
         default:
             return cudaErrorInvalidValue;

@@ -49,7 +49,7 @@ k_tile_ranges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ nu
 }
 
 template <int TS>
-__global__ void __launch_bounds__(TS * TS >= 256 ? 256 : TS * TS, blend_min_blocks<TS>())
+__global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>())
 k_blend(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, const float4* __restrict__ splats,
         const Frame f, float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib) {
     pdl_wait();
@@ -87,7 +87,7 @@ cudaError_t launch_rasterize(const uint32_t* num_keys, int64_t /*key_capacity_hi
             return launch_pdl(k_blend<16>, dim3(ntiles), dim3(256), 0, stream, r2, vals, s4, f, image, t_final,
                               n_contrib);
         case 32:
-            return launch_pdl(k_blend<32>, dim3(ntiles), dim3(256), 0, stream, r2, vals, s4, f, image, t_final,
+            return launch_pdl(k_blend<32>, dim3(ntiles), dim3(1024), 0, stream, r2, vals, s4, f, image, t_final,
                               n_contrib);
         default:
             return cudaErrorInvalidValue;
