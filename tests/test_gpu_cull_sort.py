@@ -83,6 +83,23 @@ def test_fused_cull_sort_rows_wider_than_the_digit_range():
     _same(a, b)
 
 
+@pytest.mark.parametrize("case", ["culled", "one_tile", "two_tiles"])
+def test_fused_cull_sort_degenerate_frames(case):
+    """A frame whose every splat is culled (no pairs), a 12x10 image (one
+    tile) and a 30x10 image (two tiles): the fused call gives what the two
+    calls give."""
+    scene, cam = S.small_forward()
+    scene = {k: v[:2000].copy() for k, v in scene.items()}
+    if case == "culled":
+        scene["opacity_logits"][:] = -7.0
+    else:
+        cam = dict(cam, width=12 if case == "one_tile" else 30, height=10)
+    a, b = _frames(scene, cam, key_capacity=64 * 2000)
+    _same(a, b)
+    if case == "culled":
+        assert int(a["num_keys"][0]) == 0
+
+
 def test_fused_cull_sort_uhd():
     """6,000,000 Gaussians at 3840x2160: 15 tile bits, first digit 8."""
     a, b = _frames(S.uhd_scene(), S.uhd_camera(3))
