@@ -39,6 +39,9 @@ METRICS = {"hd": METRIC, "uhd": "2160p frames/s at 6M splats"}
 # reset to None whenever that kernel changes.
 KERNEL_TRAFFIC = {("k_blend", 16): 51_944_448 + 11_329_280, ("k_blend_bwd", 16): 49_817_344 + 1_578_496,
                   ("k_train", 16): 42_897_920 + 4_633_856}
+# k_blend_bwd_batch: DRAM bytes per (tile, splat) pair from one capture of
+# the first 8 of the 64 views (a case small enough to capture), per tile size.
+BATCH_BWD_TRAFFIC_PER_PAIR = {16: (3_824_162_000 + 986_591_232) / 17_334_892}
 STAGES = ("preprocess", "cull", "sort", "rasterize")
 
 
@@ -917,7 +920,7 @@ def batch_block(args, dev, min_timed_s=1.0, plain_min_s=0.5):
     import torch
     from paper_2602_03207_gb300 import autotune, batch, capi, render, synthetic as S
     scene_np = S.batch_scene()
-    cams = S.batch_views()
+    cams = S.batch_views()[:max(1, args.views)]
     n = scene_np["means"].shape[0]
     V = len(cams)
     scene = render.scene_to_device(scene_np, dev)
@@ -951,7 +954,8 @@ def batch_block(args, dev, min_timed_s=1.0, plain_min_s=0.5):
     # the fused single-pass step, on one block per (view, tile) and on the
     # persistent grid (same results bit for bit; timed the same way)
     variants = {}
-    for name, fused, persistent in (("fused_grid", True, False), ("fused_persistent", True, True)):
+    for name, fused, persistent in (() if args.no_variants else
+                                    (("fused_grid", True, False), ("fused_persistent", True, True))):
         bv = batch.BatchRenderer(n, cams, tile=best["tile"], digit_bits=best["digit_bits"],
                                  key_capacity=best["key_capacity"], device=dev, fused=fused, persistent=persistent)
         gv = bv.capture(scene, tgt)
@@ -1005,7 +1009,7 @@ def batch_block(args, dev, min_timed_s=1.0, plain_min_s=0.5):
         "steps": steps, "ms_per_step": round(t_batch * 1e3, 3),
         "timing": {"regions": regions, "steps_per_region": steps, "statistic": "median region",
                    "region_ms": {"min": round(min(region_s) * 1e3, 3), "max": round(max(region_s) * 1e3, 3)}},
-        "config": {"workload": "2,000,000 Gaussians x 64 views 320x240..1920x1080, fwd + L2 residual + bwd",
+        "config": {"workload": f"2,000,000 Gaussians x {V} views 320x240..1920x1080, fwd + L2 residual + bwd",
                    "tile": best["tile"], "digit_bits": best["digit_bits"], "pairs": pairs,
                    "autotune": best.get("table"), "autotune_cached": best.get("cached")},
         "stages_ms": {k: round(v, 3) for k, v in stage_ms.items()},
@@ -1015,7 +1019,11 @@ def batch_block(args, dev, min_timed_s=1.0, plain_min_s=0.5):
                               "single pass per (view, tile) and its persistent grid give the same results",
         "roofline": {"kernel": f"k_blend_bwd_batch<{best['tile']}> (timed span: ws_rasterize_backward_batch)",
                      "bound": "alu", "alg_evals": int(evals), "achieved": round(ach, 3), "peak": round(peak, 2),
-                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                     "traffic": (round(BATCH_BWD_TRAFFIC_PER_PAIR[best["tile"]] * pairs)
+                                 if best["tile"] in BATCH_BWD_TRAFFIC_PER_PAIR else None),
+                     "traffic_note": "DRAM bytes per pair of an ncu capture of the 8-view batch (17,334,892 "
+                                     "pairs), times this step's pairs",
                      "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"},
         "clocks": clk.summary(),
     }
@@ -1171,6 +1179,8 @@ def main():
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batch: use --tile / --digit-bits as given")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the per-view comparison")
+    ap.add_argument("--no-variants", action="store_true", help="batch: skip the fused single-pass variants")
+    ap.add_argument("--views", type=int, default=64, help="batch: the first N of the 64 seeded views")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-views measurement")
     ap.add_argument("--no-uhd", action="store_true", help="skip the 2160p/6M per-stage table")
