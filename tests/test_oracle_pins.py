@@ -403,15 +403,26 @@ def test_emission_and_ranges():
 
 # ----------------------------------------------------------- gradient (§1)
 
-@pytest.mark.parametrize("big", [False, True])
-def test_gradient_matches_central_differences(big):
+@pytest.mark.parametrize("kind", ["small", "big", "needles"])
+def test_gradient_matches_central_differences(kind):
     """The oracle's analytic FP64 gradient of L = 1/2 ||C - target||^2 agrees
     with FP64 central differences on 64 Gaussians at 32x32 (entries whose
     step changes a discrete decision are skipped and counted). The second
-    scene uses larger, overlapping splats so occlusion terms matter."""
+    scene uses larger, overlapping splats so occlusion terms matter; the
+    third, 24 needles (one long axis, the others e^-6) in random orientations,
+    whose projected covariances have condition numbers up to ~200, so the
+    anisotropic parts of the chain (the conic of a thin ellipse, the rotation
+    gradient) carry weight."""
     scene, cam, target = S.gradcheck_scene()
-    if big:
+    if kind == "big":
         scene = S.uniform_scene(64, seed=7, log_scale_mean=-2.3, log_scale_std=0.3)
+    elif kind == "needles":
+        scene = S.uniform_scene(24, seed=8)
+        rng = np.random.default_rng(9)
+        ls = np.full((24, 3), -6.0)
+        ls[:, 0] = rng.uniform(-1.2, -0.4, 24)
+        scene["log_scales"] = ls.astype(np.float32)
+        scene["opacity_logits"] = rng.normal(0.5, 1.0, 24).astype(np.float32)
     sc = {k: v.astype(np.float64) for k, v in scene.items()}
     base = oracle.loss_grad(sc, cam, target)
     h = 1e-6
