@@ -416,6 +416,20 @@ struct BwdPixels {
     }
 };
 
+// Tile of a frame that the backward's launch index b takes: the tile rows
+// centre-out (c, c + 1, c - 1, c + 2, ..., c = (TY - 1) / 2, a bijection onto
+// [0, TY) for either parity of TY), each row left to right. The rows near
+// the image's centre, where the lists are longest in views of a centred
+// scene, start first and the short border rows fill the end of the launch;
+// neighbouring launches stay neighbouring tiles. Each tile's computation is
+// the same whatever the order.
+__device__ __forceinline__ int centre_out_tile(const Frame& f, int b) {
+    const int r = b / f.TX, tx = b - r * f.TX;
+    const int c = (f.TY - 1) / 2;
+    const int ty = (r & 1) ? c + (r + 1) / 2 : c - r / 2;
+    return ty * f.TX + tx;
+}
+
 // Emission slot of the pair (tile (tx, ty), Gaussian g): its first slot
 // slot_of(g) plus the tile's row-major rank in g's rectangle.
 template <typename SlotBase>
