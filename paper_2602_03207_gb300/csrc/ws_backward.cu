@@ -58,7 +58,7 @@ k_train(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, con
         const uint2* __restrict__ rect, const uint32_t* __restrict__ offsets, const Frame f,
         const float* __restrict__ target, float* __restrict__ image, float* __restrict__ t_final,
         uint32_t* __restrict__ n_contrib, float* __restrict__ partials) {
-    __shared__ BwdSmem<TS> sm;
+    __shared__ TrainSmem<TS> sm;
     pdl_wait();
     const int t = centre_out_tile(f, blockIdx.x);
     train_tile<TS>(f, t, ranges[t], vals, splats, rect,

@@ -134,7 +134,7 @@ k_train_batch(const uint2* __restrict__ ranges, const uint32_t* __restrict__ val
               const uint32_t* __restrict__ offsets, const FrameTable ft, const float* __restrict__ target,
               float* __restrict__ image, float* __restrict__ t_final, uint32_t* __restrict__ n_contrib,
               float* __restrict__ partials) {
-    __shared__ BwdSmem<TS> sm;
+    __shared__ TrainSmem<TS> sm;
     pdl_wait();
     const uint32_t ntiles = ft.tile_off[ft.views];
     const uint32_t stride = PERSISTENT ? gridDim.x : ntiles;

@@ -11,6 +11,10 @@ namespace ws {
 
 constexpr int kBlendBatch = 256;  // splats staged in shared memory at a time
 constexpr int kBwdChunk = 64;     // splats whose partials the backward holds at a time
+// The fused training pass holds the partials of 32 splats at a time: half the
+// partial buffer and 48 registers instead of 64 let five of its blocks share
+// an SM instead of four.
+constexpr int kTrainChunk = 32;
 constexpr int kPart = 9;          // dmean x, y; dconic a, b, c; sigma dsigma; drgb r, g, b
 
 // Blocks per SM that the forward blends are compiled for (their register
@@ -266,7 +270,7 @@ struct FwdPixels {
 // (raw = sigma G, the unclamped alpha) and dL/dpower = a dL/da with
 // power = -1/2 d^T Q d, giving d/dmean = Q d, d/dQ_a = -dx^2/2,
 // d/dQ_b = -dx dy, d/dQ_c = -dy^2/2.
-template <int TS>
+template <int TS, int CHUNK = kBwdChunk>
 struct BwdPixels {
     using G = TileGeom<TS>;
     float px[G::PPT], py[G::PPT], T[G::PPT], dC[G::PPT][3], Bc[G::PPT][3];
@@ -284,7 +288,7 @@ struct BwdPixels {
     }
 
     // Walks the staged splats [0, cnt) back to front (list positions pos0 +
-    // j), in chunks of kBwdChunk. Each half-warp visits, back to front, the
+    // j), in chunks of CHUNK. Each half-warp visits, back to front, the
     // splats whose mask has its own 4x4 sub-block; the two halves run in
     // lockstep for max(visits of either half) steps (an idle half evaluates
     // nothing). Each half sums its splat's 9 partials over its 16 pixels in
@@ -297,8 +301,8 @@ struct BwdPixels {
                                           float* __restrict__ partials) {
         const int half = lane >> 4;
         const int hw = 2 * warp + half;  // this lane's half-warp
-        for (int hi = cnt; hi > 0; hi -= kBwdChunk) {
-            const int lo = max(0, hi - kBwdChunk);
+        for (int hi = cnt; hi > 0; hi -= CHUNK) {
+            const int lo = max(0, hi - CHUNK);
             for (int j = threadIdx.x; j < hi - lo; j += G::THREADS) s_wrote[j] = 0u;
             __syncthreads();
 #pragma unroll
@@ -533,16 +537,21 @@ __device__ __forceinline__ void blend_tile(const Frame& f, int tile, uint2 range
     }
 }
 
-// Shared memory of the backward and fused kernels, staging BATCH splats.
-template <int TS, int BATCH = kBlendBatch>
+// Shared memory of the backward and fused kernels, staging BATCH splats and
+// holding the partials of CHUNK of them.
+template <int TS, int BATCH = kBlendBatch, int CHUNK = kBwdChunk>
 struct BwdSmem {
     SplatRec rec[rec_slots(BATCH)];
     typename TileGeom<TS>::Mask mask[BATCH];
     uint32_t slot[BATCH];
-    float part[kBwdChunk][2 * TileGeom<TS>::WARPS][kPart];
-    uint32_t wrote[kBwdChunk];
+    float part[CHUNK][2 * TileGeom<TS>::WARPS][kPart];
+    uint32_t wrote[CHUNK];
     uint32_t maxl[TileGeom<TS>::WARPS];
 };
+
+// Shared memory of the fused training pass.
+template <int TS>
+using TrainSmem = BwdSmem<TS, kBlendBatch, kTrainChunk>;
 
 // Backward of one tile from the stored forward outputs: each pair's 9
 // partials at its emission slot (see BwdPixels), staging kBwdChunk splats at
@@ -602,7 +611,7 @@ __device__ __forceinline__ void train_tile(const Frame& f, int tile, uint2 range
                                            SlotBase slot_of, const float* __restrict__ target,
                                            float* __restrict__ image, float* __restrict__ t_final,
                                            uint32_t* __restrict__ n_contrib, float* __restrict__ partials,
-                                           BwdSmem<TS>& sm) {
+                                           TrainSmem<TS>& sm) {
     using G = TileGeom<TS>;
     const int tx = tile % f.TX, ty = tile / f.TX;
     const float ox = (float)(tx * TS), oy = (float)(ty * TS);
@@ -611,7 +620,7 @@ __device__ __forceinline__ void train_tile(const Frame& f, int tile, uint2 range
     const uint32_t len = range.y - range.x;
     const int nb = (int)((len + kBlendBatch - 1) / kBlendBatch);
     init_null_splats(sm.rec, kBlendBatch);
-    BwdPixels<TS> B;
+    BwdPixels<TS, kTrainChunk> B;
     {
         FwdPixels<TS> P;
         P.init(warp, lane);
