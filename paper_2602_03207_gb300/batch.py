@@ -147,6 +147,12 @@ class BatchRenderer:
         self.preprocess(scene, stream)
         self.cull(stream)
         self.sort(stream)
+        return self.train_pass(scene, target, stream)
+
+    def train_pass(self, scene, target, stream=None):
+        """The fused pass of a step after the sort (ws_render_train_l2_batch):
+        images, L2 residual, backward records and the per-Gaussian gradients
+        summed over the views; one persistent grid when persistent=True."""
         g = self.grads
         capi.ws_render_train_l2_batch(self.n, scene["means"], scene["log_scales"], scene["quats"], scene["sh"],
                                       self.cams_arr, self.raster_cfg, self.num_keys, self.sorted_keys, self.sorted_vals,
