@@ -38,7 +38,7 @@ METRICS = {"hd": METRIC, "uhd": "2160p frames/s at 6M splats"}
 # training step; the captures' summaries are kept under profiles/); to be
 # reset to None whenever that kernel changes.
 KERNEL_TRAFFIC = {("k_blend", 16): 51_944_448 + 11_329_280, ("k_blend_bwd", 16): 49_844_992 + 1_542_912,
-                  ("k_train", 16): 43_032_320 + 4_728_320}
+                  ("k_train", 16): 43_082_752 + 4_845_312}
 # k_blend_bwd_batch: DRAM bytes per (tile, splat) pair from one capture of
 # the first 8 of the 64 views (a case small enough to capture), per tile size.
 BATCH_BWD_TRAFFIC_PER_PAIR = {16: (3_824_162_000 + 986_591_232) / 17_334_892}
