@@ -122,10 +122,7 @@ k_preprocess_bwd(int64_t n, const float* __restrict__ means, const float* __rest
         col[1] = cl.y;
         col[2] = cl.z;
         // slot-ordered sum of this Gaussian's pair records
-        const float* src = partials + (size_t)first * kPart;
-        for (uint32_t s = 0; s < nrec; ++s)
-#pragma unroll
-            for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
+        sum_pair_records(partials + (size_t)first * kPart, nrec, pr);
         glogit = pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
         splat_adjoint(f, X, q4, ls, pr, cl.w, gm, gls, gq);  // cl.w: the axis basis's t
     }

@@ -213,10 +213,7 @@ k_preprocess_bwd_batch(int64_t n, const float* __restrict__ means, const float* 
         // records past the key capacity were never written (the emission
         // dropped those pairs and raised WS_FLAG_CAPACITY)
         const uint32_t nrec = first >= cap ? 0u : min(cnt, cap - first);
-        const float* src = partials + (size_t)first * kPart;
-        for (uint32_t s = 0; s < nrec; ++s)
-#pragma unroll
-            for (int c = 0; c < kPart; ++c) pr[c] += __ldg(src + s * kPart + c);
+        sum_pair_records(partials + (size_t)first * kPart, nrec, pr);
         const float sig = __ldg(splats + kSplatVec4 * o + 1).w;  // sigma (the same in every view)
         glogit += pr[5] * (1.f - sig);  // pr[5] = sigma dL/dsigma
         const Frame& f = ft.f[v];

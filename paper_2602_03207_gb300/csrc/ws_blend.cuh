@@ -475,6 +475,27 @@ __device__ __forceinline__ void zero_records(uint2 range, uint32_t from, const u
     }
 }
 
+// Slot-ordered sum of a Gaussian's nrec pair records (kPart floats each,
+// contiguous from src) into pr: the loads of four records are issued before
+// their adds, and the adds keep slot order (a record past nrec adds +0, which
+// leaves a sum that started at +0 bit for bit unchanged), so the result is
+// that of the plain loop with a quarter of its dependent load latencies.
+__device__ __forceinline__ void sum_pair_records(const float* __restrict__ src, uint32_t nrec, float (&pr)[kPart]) {
+    for (uint32_t s = 0; s < nrec; s += 4) {
+        float r[4][kPart];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool ok = s + k < nrec;
+#pragma unroll
+            for (int c = 0; c < kPart; ++c) r[k][c] = ok ? __ldg(src + (size_t)(s + k) * kPart + c) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int c = 0; c < kPart; ++c) pr[c] += r[k][c];
+    }
+}
+
 // Stages list positions [start, start + cnt) of a tile: records and masks,
 // and (WITH_SLOT) each pair's emission slot. The stagings of the backward
 // and of the fused training pass (WITH_SLOT) build the ellipse's sub-block
