@@ -13,12 +13,12 @@ pytestmark = pytest.mark.gpu
 NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
-def gpu_grads(scene_np, cam, target, tile=16, key_capacity=None):
+def gpu_grads(scene_np, cam, target, tile=16, key_capacity=None, flags=0):
     import torch
     from paper_2602_03207_gb300 import render
     dev = render.scene_to_device(scene_np)
     n = scene_np["means"].shape[0]
-    r = render.Renderer(n, cam["width"], cam["height"], tile=tile, key_capacity=key_capacity)
+    r = render.Renderer(n, cam["width"], cam["height"], tile=tile, key_capacity=key_capacity, flags=flags)
     img = r.forward(dev, cam)
     r.check_status()
     d_img = img - torch.as_tensor(target, device=img.device)
@@ -51,6 +51,35 @@ def test_gradients_tile_sizes(tile):
     ref = oracle.loss_grad(sub, cam, target, tile=tile)["grads"]
     for k in NAMES:
         assert rel(g[k], ref[k].reshape(g[k].shape)) <= 1e-3, k
+
+
+@pytest.mark.parametrize("flags", [1, 2, 8, 11])
+def test_gradients_under_ablation_flags(flags):
+    """The §4.4 ablations (1: keep sigma < 1/255, 2: -CULL keeps off-screen
+    boxes, 8: -RADIUS opacity-independent box) only add pairs whose alpha is
+    below 1/255 at every pixel: their records are zeros, added in slot order
+    to sums that start at +0, so the gradients equal the default's bit for
+    bit; and they match the oracle's gradient under the same flag."""
+    scene = S.uniform_scene(2000, seed=53)
+    scene["opacity_logits"][:200] = -7.0
+    cam = S.look_at_camera((2.2, -1.0, 0.8), (0.4, 0.0, 0.0), 96, 72)
+    target = np.random.default_rng(14).random((72, 96, 3)).astype(np.float32)
+    import torch
+    from paper_2602_03207_gb300 import render
+    g, img = gpu_grads(scene, cam, target, key_capacity=60 * 2000, flags=flags)
+    base, base_img = gpu_grads(scene, cam, target, key_capacity=60 * 2000)
+    np.testing.assert_array_equal(img, base_img)
+    for k in NAMES:
+        np.testing.assert_array_equal(g[k], base[k])
+    # the fused training pass under the same flag
+    r = render.Renderer(2000, 96, 72, key_capacity=60 * 2000, flags=flags)
+    gf = r.train_step_l2(render.scene_to_device(scene), cam, torch.as_tensor(target, device="cuda"))
+    r.check_status()
+    for k in NAMES:
+        np.testing.assert_array_equal(gf[k].cpu().numpy().astype(np.float64), base[k])
+    ref = oracle.loss_grad(scene, cam, target, flags=flags)["grads"]
+    for k in NAMES:
+        assert rel(g[k], ref[k].reshape(g[k].shape)) <= 1e-3, (k, rel(g[k], ref[k].reshape(g[k].shape)))
 
 
 def test_gradients_deterministic():
