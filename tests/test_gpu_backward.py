@@ -82,6 +82,32 @@ def test_gradients_under_ablation_flags(flags):
         assert rel(g[k], ref[k].reshape(g[k].shape)) <= 1e-3, (k, rel(g[k], ref[k].reshape(g[k].shape)))
 
 
+def test_gradients_of_empty_and_fully_culled_scenes():
+    """n = 0 (empty gradient arrays) and a scene whose every splat is below
+    1/255 (no pair at all): the image is the background, the separate calls
+    and the fused pass give all-zero gradients, as the oracle does."""
+    import torch
+    from paper_2602_03207_gb300 import render
+    cam = dict(S.small_forward()[1])
+    cam["bg"] = (0.25, 0.5, 0.75)
+    target = np.random.default_rng(15).random((256, 256, 3)).astype(np.float32)
+    empty = S.uniform_scene(0, seed=1)
+    g, img = gpu_grads(empty, cam, target)
+    np.testing.assert_array_equal(img, np.broadcast_to(np.float32(cam["bg"]), img.shape))
+    assert all(g[k].size == 0 for k in NAMES)
+    scene = S.uniform_scene(500, seed=2)
+    scene["opacity_logits"][:] = -7.0
+    g, img = gpu_grads(scene, cam, target)
+    np.testing.assert_array_equal(img, np.broadcast_to(np.float32(cam["bg"]), img.shape))
+    r = render.Renderer(500, 256, 256)
+    gf = r.train_step_l2(render.scene_to_device(scene), cam, torch.as_tensor(target, device="cuda"))
+    r.check_status()
+    ref = oracle.loss_grad(scene, cam, target)["grads"]
+    for k in NAMES:
+        assert not np.any(g[k]) and not np.any(gf[k].cpu().numpy()), k
+        assert not np.any(ref[k]), k
+
+
 def test_gradients_deterministic():
     scene, cam = S.small_forward()
     target = np.random.default_rng(10).random((256, 256, 3)).astype(np.float32)
