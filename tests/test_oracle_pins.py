@@ -469,6 +469,25 @@ def test_ablations_leave_the_image_unchanged():
         assert out["keys"].size > base["keys"].size
 
 
+def test_ablations_leave_the_gradient_unchanged():
+    """The same ablations leave the loss and its analytic gradient unchanged:
+    an added pair's alpha is below 1/255 at every pixel, so it is never
+    composited and its partials are zero (a mistake that let the flags reach
+    the adjoint, e.g. a gradient through the fixed radius, would show here)."""
+    scene = S.uniform_scene(600, seed=51)
+    scene["opacity_logits"][:60] = -7.0
+    cam = S.look_at_camera((2.2, -1.0, 0.8), (0.4, 0.0, 0.0), 64, 48)
+    target = np.random.default_rng(16).random((48, 64, 3))
+    base = oracle.loss_grad(scene, cam, target)
+    assert np.linalg.norm(base["grads"]["means"]) > 0
+    for flags in (oracle.NO_OPACITY_CULL, oracle.NO_AABB_CULL, oracle.FIXED_RADIUS,
+                  oracle.NO_OPACITY_CULL | oracle.NO_AABB_CULL | oracle.FIXED_RADIUS):
+        out = oracle.loss_grad(scene, cam, target, flags=flags)
+        assert abs(out["loss"] - base["loss"]) <= 1e-12 * abs(base["loss"])
+        for k, g in base["grads"].items():
+            np.testing.assert_allclose(out["grads"][k], g, rtol=0, atol=1e-12 * max(1.0, np.abs(g).max()))
+
+
 # ------------------------------------------------------------ packed record
 
 def test_f16_rounding_is_ieee_binary16():
