@@ -135,7 +135,7 @@ class BatchRenderer:
     def step(self, scene, target, stream=None):
         """One training step of 1/2 ||image - target||^2 summed over the views.
         Default: the separate calls (forward, d_image = image - target,
-        backward), the fastest on GB300. fused=True: pre-processing,
+        backward). fused=True (about 1.5 % faster on GB300): pre-processing,
         compaction, sort, then ws_render_train_l2_batch (every (view, tile)
         composited, its residual formed and its backward records written in
         one pass; persistent=True runs that pass as one persistent grid). All
