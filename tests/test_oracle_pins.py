@@ -341,7 +341,7 @@ def test_tile_lists_equal_brute_force_back_to_front():
     cam = {"viewmat": np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 3]], np.float32),
            "fx": 40.0, "fy": 40.0, "cx": 24.0, "cy": 20.0, "width": 48, "height": 40,
            "znear": 0.2, "bg": (0.1, 0.2, 0.3)}
-    for tile in (8, 16):
+    for tile in (8, 16, 32):
         out = oracle.render(scene, cam, tile=tile)
         img, tf = oracle.blend_brute(cam, out["proj"])
         ok = out["n_amb"] == 0
@@ -467,6 +467,23 @@ def test_ablations_leave_the_image_unchanged():
         ok = (base["n_amb"] == 0) & (out["n_amb"] == 0)
         np.testing.assert_allclose(out["image"][ok], base["image"][ok], atol=1e-14)
         assert out["keys"].size > base["keys"].size
+
+
+def test_gradient_does_not_depend_on_the_tile_size():
+    """The tile decomposition is a schedule, not part of the method: the loss
+    and the analytic gradient for 8-, 16- and 32-pixel tiles agree to FP64
+    rounding (a tile-dependent pixel coordinate, list or sum in the backward
+    would show here)."""
+    scene = S.uniform_scene(400, seed=22)
+    cam = S.look_at_camera((2.0, -1.2, 0.9), (0.3, 0.1, 0.0), 72, 56)
+    target = np.random.default_rng(17).random((56, 72, 3))
+    base = oracle.loss_grad(scene, cam, target, tile=16)
+    assert np.linalg.norm(base["grads"]["means"]) > 0
+    for tile in (8, 32):
+        out = oracle.loss_grad(scene, cam, target, tile=tile)
+        assert abs(out["loss"] - base["loss"]) <= 1e-12 * abs(base["loss"])
+        for k, g in base["grads"].items():
+            np.testing.assert_allclose(out["grads"][k], g, rtol=0, atol=1e-12 * max(1.0, np.abs(g).max()))
 
 
 def test_ablations_leave_the_gradient_unchanged():
