@@ -469,6 +469,60 @@ def test_ablations_leave_the_image_unchanged():
         assert out["keys"].size > base["keys"].size
 
 
+def _fd_check(sc, cam, target, names, h=1e-6):
+    """Analytic FP64 gradient against central differences on the named
+    parameters (entries whose step changes a discrete decision skipped)."""
+    base = oracle.loss_grad(sc, cam, target)
+    for name in names:
+        flat = sc[name].reshape(-1)
+        g = base["grads"][name].reshape(-1)
+        for j in range(flat.size):
+            old = flat[j]
+            flat[j] = old + h
+            p = oracle.loss_grad(sc, cam, target, grads=False)
+            flat[j] = old - h
+            m = oracle.loss_grad(sc, cam, target, grads=False)
+            flat[j] = old
+            if p["fingerprint"] != base["fingerprint"] or m["fingerprint"] != base["fingerprint"]:
+                continue
+            fd = (p["loss"] - m["loss"]) / (2 * h)
+            assert abs(g[j] - fd) <= 1e-6 * max(1.0, abs(fd)), (name, j, g[j], fd)
+    return base
+
+
+def test_no_gradient_through_the_clamps():
+    """Reading 12: a colour channel clamped at 0 passes no gradient to its SH
+    coefficients, and an alpha clamped at 0.99 none to the splat's opacity
+    or shape from that pixel; the analytic values agree with central
+    differences there (a gradient taken through either clamp would not)."""
+    sh = np.zeros((2, 16, 3))
+    sh[:, 0, :] = 0.3 / C0  # colour 0.8
+    sh[0, 0, 0] = -2.0 / C0  # red of splat 0: 0.5 - 2 + small terms < 0, clamped
+    sh[0, 1:4, 0] = [0.05, -0.03, 0.02]
+    # splat 1 centred on the centre of pixel (16, 16) at sigma ~ 0.9997
+    z1 = 5.0
+    means = [[0.3, -0.2, 4.0], [0.5 * z1 / 32.0, 0.5 * z1 / 32.0, z1]]
+    sc = _scene(2, means, [[-1.6] * 3, [-1.5] * 3], logits=[1.0, 8.0], sh=sh)
+    cam = _cam(32, 32, 32.0)
+    # the 0.99 clamp is active: splat 1 alone gives C = 0.8 * 0.99 at its centre
+    one = {k: v[1:] for k, v in sc.items()}
+    out = oracle.render(one, cam)
+    np.testing.assert_allclose(out["image"][16, 16], [0.8 * 0.99] * 3, rtol=1e-12)
+    target = np.random.default_rng(18).random((32, 32, 3))
+    base = _fd_check(sc, cam, target, ("opacity_logits", "log_scales", "sh"))
+    g = base["grads"]["sh"]
+    assert not np.any(g[0, :, 0])  # the clamped channel
+    assert np.all(g[0, 0, 1:] != 0) and np.all(g[1, 0, :] != 0)
+    # splat 1 alone: its clamped centre pixel adds nothing to the opacity
+    # gradient, so a target that matches the image everywhere else gives 0
+    img = oracle.render(one, cam)["image"]
+    tgt = img.copy()
+    tgt[16, 16] += 0.25
+    g1 = oracle.loss_grad(one, cam, tgt)["grads"]
+    assert g1["opacity_logits"][0] == 0 and not np.any(g1["log_scales"]) and not np.any(g1["means"])
+    assert np.any(g1["sh"])  # the colour still gets the residual of that pixel
+
+
 def test_gradient_does_not_depend_on_the_tile_size():
     """The tile decomposition is a schedule, not part of the method: the loss
     and the analytic gradient for 8-, 16- and 32-pixel tiles agree to FP64
