@@ -523,6 +523,26 @@ def test_no_gradient_through_the_clamps():
     assert np.any(g1["sh"])  # the colour still gets the residual of that pixel
 
 
+def test_gradient_with_the_guard_band_clamp_active():
+    """Reading 2 / 12: a splat whose centre lies beyond the 1.3x guard band
+    (t_x / t_z = 0.8 against a limit of 0.65 here) has its Jacobian built
+    from the clamped ratio, and the analytic gradient, which passes nothing
+    through the clamped ratio, agrees with central differences; the splat
+    still reaches into the image, so its gradient is not zero."""
+    sh = np.zeros((2, 16, 3))
+    sh[:, 0, :] = 0.3 / C0
+    sh[0, 1:4, :] = 0.1  # view-dependent colour: the direction term as well
+    means = [[0.8 * 4.0, 0.1, 4.0], [-0.2, 0.1, 5.0]]
+    sc = _scene(2, means, [[0.0, -0.3, -0.6], [-1.8] * 3], logits=[1.5, 0.5], sh=sh,
+                quats=[[0.9, 0.1, 0.3, -0.2], [1.0, 0.0, 0.0, 0.0]])
+    cam = _cam(32, 32, 32.0)
+    out = oracle.render(sc, cam)
+    assert out["proj"]["touched"][0] > 0 and out["proj"]["mean2d"][0][0] > 32  # centre off-screen
+    target = np.random.default_rng(19).random((32, 32, 3))
+    base = _fd_check(sc, cam, target, ("means", "log_scales", "quats", "opacity_logits"))
+    assert np.linalg.norm(base["grads"]["means"][0]) > 0
+
+
 def test_gradient_does_not_depend_on_the_tile_size():
     """The tile decomposition is a schedule, not part of the method: the loss
     and the analytic gradient for 8-, 16- and 32-pixel tiles agree to FP64
