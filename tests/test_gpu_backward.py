@@ -42,6 +42,24 @@ def test_gradients_match_oracle_small(big):
         assert rel(g[k], ref[k].reshape(g[k].shape)) <= 1e-3, (k, rel(g[k], ref[k].reshape(g[k].shape)))
 
 
+def test_gradients_with_a_background():
+    """A non-black background enters every pair's alpha derivative through
+    the colour behind it (the backward starts that colour at the background):
+    the separate calls and the fused pass against the oracle's gradient."""
+    import torch
+    from paper_2602_03207_gb300 import render
+    scene, cam, target = S.gradcheck_scene()
+    cam = dict(cam, bg=(0.3, 0.6, 0.9))
+    g, _ = gpu_grads(scene, cam, target)
+    r = render.Renderer(64, 32, 32)
+    gf = r.train_step_l2(render.scene_to_device(scene), cam, torch.as_tensor(target, device="cuda"))
+    r.check_status()
+    ref = oracle.loss_grad(scene, cam, target)["grads"]
+    for k in NAMES:
+        assert rel(g[k], ref[k].reshape(g[k].shape)) <= 1e-3, (k, rel(g[k], ref[k].reshape(g[k].shape)))
+        np.testing.assert_array_equal(gf[k].cpu().numpy().astype(np.float64), g[k])
+
+
 @pytest.mark.parametrize("tile", [8, 32])
 def test_gradients_tile_sizes(tile):
     scene, cam = S.small_forward()
