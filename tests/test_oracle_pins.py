@@ -199,6 +199,27 @@ def test_isotropic_off_axis_closed_form():
     np.testing.assert_allclose(p["cov2d"][0, 0], k * (1 + 0.65 ** 2) + 0.3, rtol=1e-12)
 
 
+def test_dilation_and_guard_band_are_taken_from_the_configuration():
+    """Reading 2: the low-pass dilation and the guard band are configuration
+    values, not constants: on-axis Sigma' = ((f s / z)^2 + dilation) I for
+    dilations 0 and 1; with a guard band of 2 the ratio x/z = 2 is clamped
+    to 2 (W/2)/f = 1 inside J, and x/z = 0.75, which the default band of 1.3
+    clamps to 0.65, is not clamped."""
+    z, s, f = 4.0, 0.05, 64.0
+    k = (f * s / z) ** 2
+    for dil in (0.0, 1.0):
+        p = oracle.preprocess(_scene(1, [0, 0, z], [math.log(s)] * 3), _cam(f=f), dilation=dil)
+        np.testing.assert_allclose(p["cov2d"][0], [k + dil, 0, k + dil], rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(p["conic"][0], [1 / (k + dil), 0, 1 / (k + dil)], rtol=1e-13)
+    p = oracle.preprocess(_scene(1, [8.0, 0, z], [math.log(s)] * 3), _cam(f=f), guard=2.0)
+    np.testing.assert_allclose(p["cov2d"][0, 0], k * (1 + 1.0 ** 2) + 0.3, rtol=1e-12)
+    sc = _scene(1, [3.0, 0, z], [math.log(s)] * 3)
+    p = oracle.preprocess(sc, _cam(f=f), guard=2.0)
+    np.testing.assert_allclose(p["cov2d"][0, 0], k * (1 + 0.75 ** 2) + 0.3, rtol=1e-12)
+    p = oracle.preprocess(sc, _cam(f=f))
+    np.testing.assert_allclose(p["cov2d"][0, 0], k * (1 + 0.65 ** 2) + 0.3, rtol=1e-12)
+
+
 def test_general_covariance_against_numerical_jacobian():
     """Sigma' = J W Sigma W^T J^T + 0.3 I for a rotated anisotropic Gaussian and
     a look-at camera, checked against an independent route: scipy's quaternion
