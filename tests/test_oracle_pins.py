@@ -226,7 +226,14 @@ def test_general_covariance_against_numerical_jacobian():
     rotation and a central-difference Jacobian of the pinhole map."""
     from scipy.spatial.transform import Rotation
     rng = np.random.default_rng(13)
-    cam = S.look_at_camera((3.0, -2.0, 1.5), (0.1, 0.2, 0.0), 96, 80, fov_x_deg=50)
+    cam0 = S.look_at_camera((3.0, -2.0, 1.5), (0.1, 0.2, 0.0), 96, 80, fov_x_deg=50)
+    # and a camera with fx != fy and an off-centre principal point
+    cam1 = dict(cam0, fx=110.0, fy=80.0, cx=41.0, cy=46.5)
+    for cam in (cam0, cam1):
+        _check_covariance_against_numerical_jacobian(cam, rng, Rotation)
+
+
+def _check_covariance_against_numerical_jacobian(cam, rng, Rotation):
     vm = np.asarray(cam["viewmat"], float)
     Rv, tv = vm[:, :3], vm[:, 3]
 
